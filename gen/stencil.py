@@ -1,0 +1,223 @@
+"""Finite-difference convection-diffusion test matrices and right-hand sides.
+
+The paper's test problems (Section 5) are Galeri stencils (BentPipe2D, UniFlow2D,
+Laplace3D, Stretched2D) and SuiteSparse matrices, none of which ship here.  The
+stand-ins built below have the same shape: 5-point (2D) and 7-point (3D)
+operators, 5 and 7 nonzeros per interior row, nonsymmetric when the wind is
+nonzero, CSR with int32 indices and FP64 values (the paper's storage, Section
+5.5).
+
+Operator: -div(K grad u) + beta . grad u on the unit square/cube with zero
+Dirichlet boundary, grid spacing h = 1/(side+1), K = diag(1, eps, 1) (eps =
+1/anisotropy on the second axis), beta = Pe * unit wind, first-order upwind
+convection.  Every row is multiplied by h^2, so for axis k
+
+    coefficient of u[i - e_k] = -K_k - h * max(beta_k, 0)
+    coefficient of u[i + e_k] = -K_k - h * max(-beta_k, 0)
+    diagonal                  = sum_k (2 K_k + h |beta_k|)
+
+which is a weakly diagonally dominant M-matrix.  Unknowns are numbered
+lexicographically with the first axis fastest, and the columns of each row come
+out sorted.
+
+Random numbers come from numpy's PCG64 generator seeded per call.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class Problem:
+    """A CSR matrix plus descriptive metadata (no right-hand side)."""
+
+    name: str
+    n: int
+    row_ptr: np.ndarray  # int32, n+1
+    col_idx: np.ndarray  # int32, nnz
+    vals: np.ndarray  # float64, nnz
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.vals, self.col_idx, self.row_ptr), shape=(self.n, self.n))
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _conv_diff(dims: tuple[int, ...], kdiag: tuple[float, ...], beta: tuple[float, ...],
+               name: str, meta: dict) -> Problem:
+    d = len(dims)
+    side = dims[0]
+    if any(s != side for s in dims):
+        raise ValueError("only cubic grids are generated")
+    n = int(np.prod(dims))
+    if n >= 2**31 - 1:
+        raise ValueError("int32 CSR indices overflow")
+    h = 1.0 / (side + 1)
+    strides = [int(np.prod(dims[:k])) for k in range(d)]
+    i = np.arange(n, dtype=np.int64)
+    coord = [(i // strides[k]) % dims[k] for k in range(d)]
+
+    # Column slots in increasing column order: -e_{d-1}, ..., -e_0, diag, +e_0, ..., +e_{d-1}.
+    slots = 2 * d + 1
+    cols = np.empty((n, slots), dtype=np.int64)
+    vals = np.empty((n, slots), dtype=np.float64)
+    mask = np.ones((n, slots), dtype=bool)
+    diag = sum(2.0 * kdiag[k] + h * abs(beta[k]) for k in range(d))
+    for s, k in enumerate(reversed(range(d))):
+        cols[:, s] = i - strides[k]
+        vals[:, s] = -kdiag[k] - h * max(beta[k], 0.0)
+        mask[:, s] = coord[k] > 0
+    cols[:, d] = i
+    vals[:, d] = diag
+    for k in range(d):
+        s = d + 1 + k
+        cols[:, s] = i + strides[k]
+        vals[:, s] = -kdiag[k] - h * max(-beta[k], 0.0)
+        mask[:, s] = coord[k] < dims[k] - 1
+
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col_idx = cols[mask].astype(np.int32)
+    v = vals[mask]
+    meta = dict(meta)
+    meta.update(dims=list(dims), h=h, K=list(kdiag), beta=list(beta),
+                cell_peclet=float(max(abs(b) for b in beta) * h / 2.0))
+    return Problem(name=name, n=n, row_ptr=row_ptr.astype(np.int32), col_idx=col_idx,
+                   vals=v, meta=meta)
+
+
+def conv_diff_2d(side: int, peclet: float = 0.0, wind=(1.0, 0.0), anisotropy: float = 1.0,
+                 name: str | None = None) -> Problem:
+    """5-point upwind convection-diffusion on a side x side grid."""
+    w = np.asarray(wind, dtype=np.float64)
+    w = w / np.linalg.norm(w) if np.linalg.norm(w) > 0 else w
+    beta = tuple(float(peclet * c) for c in w)
+    kd = (1.0, 1.0 / anisotropy)
+    nm = name or f"convdiff2d_{side}"
+    return _conv_diff((side, side), kd, beta, nm,
+                      dict(peclet=peclet, wind=list(map(float, w)), anisotropy=anisotropy))
+
+
+def conv_diff_3d(side: int, peclet: float = 0.0, wind=(1.0, 0.0, 0.0), anisotropy: float = 1.0,
+                 name: str | None = None) -> Problem:
+    """7-point upwind convection-diffusion on a side^3 grid."""
+    w = np.asarray(wind, dtype=np.float64)
+    w = w / np.linalg.norm(w) if np.linalg.norm(w) > 0 else w
+    beta = tuple(float(peclet * c) for c in w)
+    kd = (1.0, 1.0 / anisotropy, 1.0)
+    nm = name or f"convdiff3d_{side}"
+    return _conv_diff((side, side, side), kd, beta, nm,
+                      dict(peclet=peclet, wind=list(map(float, w)), anisotropy=anisotropy))
+
+
+def random_wind(seed: int, dim: int) -> np.ndarray:
+    """Unit wind direction: angle ~ U(0, 2pi) in 2D, uniform on the sphere in 3D."""
+    g = _rng(seed)
+    if dim == 2:
+        phi = g.uniform(0.0, 2.0 * np.pi)
+        return np.array([np.cos(phi), np.sin(phi)])
+    v = g.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+def rhs_manufactured(p: Problem, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """x_true ~ U(-1, 1) from the seed and b = A x_true (FP64)."""
+    x_true = _rng(seed).uniform(-1.0, 1.0, p.n)
+    return p.scipy() @ x_true, x_true
+
+
+def rhs_ones(p: Problem) -> np.ndarray:
+    return np.ones(p.n)
+
+
+def rhs_ones_plus_noise(p: Problem, seed: int, sigma: float = 1e-3) -> np.ndarray:
+    """b = A * ones + sigma * N(0, 1)."""
+    return p.scipy() @ np.ones(p.n) + sigma * _rng(seed).standard_normal(p.n)
+
+
+# --------------------------------------------------------------------------
+# Workload recipes (sizes and seeds of the five workloads).
+# --------------------------------------------------------------------------
+
+def config_small_2d(side: int = 64):
+    """64x64 5-point convection-diffusion, Pe 10, random wind (seed 101), manufactured
+    solution x_true ~ U(-1,1) (seed 102)."""
+    p = conv_diff_2d(side, 10.0, random_wind(101, 2), name=f"convdiff2d_{side}_pe10")
+    b, x_true = rhs_manufactured(p, 102)
+    return p, b, x_true
+
+
+def config_3d(peclet: float = 10.0, side: int = 100):
+    """100^3 7-point convection-diffusion; Pe in {1, 10, 50} picks wind seed 201/202/203 and
+    noise seed 211/212/213; b = A*1 + 1e-3 N(0,1)."""
+    table = {1.0: (201, 211), 10.0: (202, 212), 50.0: (203, 213)}
+    ws, rs = table.get(float(peclet), (200 + int(peclet), 210 + int(peclet)))
+    p = conv_diff_3d(side, peclet, random_wind(ws, 3), name=f"convdiff3d_{side}_pe{peclet:g}")
+    return p, rhs_ones_plus_noise(p, rs)
+
+
+def config_aniso_2d(side: int = 2000, anisotropy: float = 100.0, peclet: float = 100.0):
+    """2000^2 anisotropic 5-point convection-diffusion, eps = 1e-2, Pe 100, wind (1,1)/sqrt(2),
+    b = ones."""
+    p = conv_diff_2d(side, peclet, (1.0, 1.0), anisotropy,
+                     name=f"aniso2d_{side}_a{anisotropy:g}_pe{peclet:g}")
+    return p, rhs_ones(p)
+
+
+def batched_systems(count: int = 512, seed0: int = 5000, side_lo: int = 32, side_hi: int = 256):
+    """Uneven batch: system s uses seed seed0+s; side ~ U{side_lo..side_hi}, Pe ~ U(0.1, 50),
+    wind angle ~ U(0, 2pi), x_true ~ U(-1, 1), b = A x_true."""
+    out = []
+    for s in range(count):
+        g = _rng(seed0 + s)
+        side = int(g.integers(side_lo, side_hi + 1))
+        pe = float(g.uniform(0.1, 50.0))
+        phi = float(g.uniform(0.0, 2.0 * np.pi))
+        p = conv_diff_2d(side, pe, (np.cos(phi), np.sin(phi)), name=f"batch{s}_{side}")
+        x_true = g.uniform(-1.0, 1.0, p.n)
+        out.append((p, p.scipy() @ x_true, x_true))
+    return out
+
+
+def selector_matrices(count: int = 400, seed0: int = 4000, n_lo: float = 1e4, n_hi: float = 4e6):
+    """Parameter-selector corpus descriptors (built lazily: large ones are up to 4M unknowns).
+
+    Matrix s uses seed seed0+s: dim 2 or 3 (50:50), Pe log-uniform [0.1, 100], anisotropy
+    log-uniform [1, 1e3], N log-uniform [n_lo, n_hi], side = round(N^(1/dim)), wind random.
+    Returns a list of dicts; build one with `build_selector_matrix`."""
+    out = []
+    for s in range(count):
+        g = _rng(seed0 + s)
+        dim = 2 if g.uniform() < 0.5 else 3
+        pe = float(10 ** g.uniform(-1.0, 2.0))
+        an = float(10 ** g.uniform(0.0, 3.0))
+        nn = float(10 ** g.uniform(np.log10(n_lo), np.log10(n_hi)))
+        side = max(4, int(round(nn ** (1.0 / dim))))
+        if dim == 2:
+            phi = float(g.uniform(0.0, 2.0 * np.pi))
+            wind = [np.cos(phi), np.sin(phi)]
+        else:
+            v = g.standard_normal(3)
+            wind = list(v / np.linalg.norm(v))
+        out.append(dict(index=s, seed=seed0 + s, dim=dim, peclet=pe, anisotropy=an,
+                        side=side, wind=wind))
+    return out
+
+
+def build_selector_matrix(desc: dict) -> Problem:
+    if desc["dim"] == 2:
+        return conv_diff_2d(desc["side"], desc["peclet"], desc["wind"], desc["anisotropy"],
+                            name=f"sel{desc['index']}")
+    return conv_diff_3d(desc["side"], desc["peclet"], desc["wind"], desc["anisotropy"],
+                        name=f"sel{desc['index']}")
