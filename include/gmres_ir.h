@@ -1,0 +1,168 @@
+/*
+ * gmres_ir.h -- C ABI of the B300 (sm_103a) mixed-precision GMRES library.
+ *
+ * Method: Loe, Glusa, Yamazaki, Boman, Rajamanickam, "A Study of Mixed
+ * Precision Strategies for GMRES on GPUs" (arXiv 2109.01232).
+ *   - gmres_solve     : restarted GMRES(m) with CGS2 orthogonalisation in FP64
+ *                       (Algorithm 1; CGS2 as described in Section 3.1).
+ *   - gmres_ir_solve  : GMRES-IR (Algorithm 2, Section 3.2): FP64 residual and
+ *                       update around a low-precision GMRES(m) cycle.
+ *   - polynomial      : right preconditioning with the GMRES polynomial,
+ *                       M^{-1} = p(A) (Section 3.4).
+ * The problem statement is that of Algorithm 1: A in R^{n x n} (CSR), b, an
+ * initial guess x0 and a relative residual tolerance; the output is x with
+ * ||b - A x||_2 / ||b||_2 <= rtol.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named as DEVICE are device memory owned by the caller; the
+ *     library never frees them.  HOST pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous in their kernel launches but return only after the final
+ *     status has been read back, so results are ready when a call returns.
+ *   - Nothing is printed and nothing throws across the ABI: every function
+ *     returns a gmres_status code.  Invalid arguments are rejected with
+ *     GMRES_ERR_INVALID before any launch.
+ *   - The library allocates its own workspace (Krylov basis, low-precision
+ *     copy of A, Hessenberg data) with cudaMalloc; plans keep it between
+ *     solves, the one-shot calls free it before returning.
+ *   - Matrices use int32 indices: n < 2^31 and nnz < 2^31.  Column indices
+ *     must lie in [0, n) and row_ptr must be nondecreasing with row_ptr[0] = 0
+ *     (checked on the device before the first solve; violations give
+ *     GMRES_ERR_INVALID).
+ */
+#ifndef GMRES_IR_H
+#define GMRES_IR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  GMRES_OK = 0,              /* converged: ||b - A x|| / ||b|| <= rtol (explicit FP64 residual) */
+  GMRES_NOT_CONVERGED = 1,   /* max_iters reached; x holds the last iterate */
+  GMRES_BREAKDOWN = 2,       /* singular least-squares factor after a breakdown (A singular) */
+  GMRES_NONFINITE = 3,       /* NaN/Inf met in A, b or a reduction */
+  GMRES_ERR_INVALID = 4,     /* bad argument (null pointer, size, parameter, CSR structure) */
+  GMRES_ERR_OOM = 5,         /* device allocation failed */
+  GMRES_ERR_CUDA = 6,        /* any other CUDA runtime error */
+  GMRES_ERR_TOO_LARGE = 7    /* a size exceeds a documented maximum */
+} gmres_status;
+
+/* Storage precision of the inner solve: the Krylov basis V and the copy of A
+ * used by the inner SpMV.  FP16/BF16 store 16-bit values and accumulate in
+ * FP32; FP16 scales A by 1/max|a_ij| and each basis vector by sqrt(n). */
+typedef enum { GMRES_FP64 = 0, GMRES_FP32 = 1, GMRES_FP16 = 2, GMRES_BF16 = 3 } gmres_prec;
+
+/* CSR matrix, FP64 values (the master copy used by every FP64 residual).
+ * All three arrays are DEVICE pointers, caller-owned, read only. */
+typedef struct {
+  int32_t n;                /* rows = columns */
+  int32_t nnz;              /* row_ptr[n] */
+  const int32_t* row_ptr;   /* n+1 entries */
+  const int32_t* col_idx;   /* nnz entries */
+  const double* vals;       /* nnz entries */
+} gmres_csr;
+
+/* Solver parameters; gmres_default_params() fills the paper's defaults
+ * (Section 5: m = 50, rtol = 1e-10, FP32 inner precision, no preconditioner). */
+typedef struct {
+  int32_t restart_m;        /* m: Arnoldi steps per cycle, 1..GMRES_MAX_RESTART */
+  double rtol;              /* outer relative residual tolerance (explicit FP64 residual) */
+  double inner_rtol;        /* IR: end an inner cycle once |g_{j+1}| <= inner_rtol * ||r||;
+                               0 = always m steps (the paper's GMRES-IR) */
+  int64_t max_iters;        /* cap on the total number of Arnoldi steps */
+  int32_t inner_prec;       /* gmres_prec of the inner cycle (IR only) */
+  int32_t poly_degree;      /* degree d of the GMRES polynomial preconditioner; 0 = none */
+  uint64_t seed;            /* SplitMix64 seed of the polynomial's start vector */
+  int32_t record_history;   /* nonzero: keep |g_{j+1}| per iteration in gmres_stats */
+} gmres_params;
+
+#define GMRES_MAX_RESTART 512
+#define GMRES_MAX_POLY_DEGREE 96
+
+/* Solve statistics (written by every solve entry point when non-NULL). */
+typedef struct {
+  int32_t status;           /* gmres_status of the solve */
+  int64_t iters;            /* total Arnoldi steps (inner iterations) */
+  int32_t outer_iters;      /* restarts = refinement steps */
+  double rel_resid;         /* final explicit ||b - A x||_2 / ||b||_2 in FP64 */
+  double t_solve_ms;        /* device time of the solve (CUDA events) */
+  double t_setup_ms;        /* device time of set-up: low-precision copy of A, polynomial */
+  int64_t history_len;      /* entries written to history (<= history_cap) */
+  double* history;          /* HOST buffer supplied by the caller, or NULL: relative
+                               residual estimate after every Arnoldi step */
+  int64_t history_cap;      /* capacity of history */
+} gmres_stats;
+
+void gmres_default_params(gmres_params* p);
+const char* gmres_status_string(int status);
+
+/* FP64 restarted GMRES(m) (Algorithm 1 with CGS2).  b: DEVICE, n doubles.
+ * x: DEVICE, n doubles, initial guess on entry, solution on exit.  The cycle
+ * ends early when the Givens residual reaches rtol*||b||; convergence is then
+ * confirmed by the explicit residual.  p->inner_prec is ignored. */
+int gmres_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                gmres_stats* stats, void* stream);
+
+/* GMRES-IR (Algorithm 2): r = b - A x [FP64]; u = GMRES(m) cycle on A u = r in
+ * p->inner_prec; x += u [FP64]; repeat while ||r|| / ||b|| > rtol.  Same
+ * pointer conventions as gmres_solve. */
+int gmres_ir_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                   gmres_stats* stats, void* stream);
+
+/* Same solves with HOST pointers: A's arrays, b and x live in host memory
+ * (pinned memory gives the fastest copies).  The call copies A, b and x0 to
+ * the device, solves, and copies x back before returning. */
+int gmres_ir_solve_host(const gmres_csr* A_host, const double* b, double* x,
+                        const gmres_params* p, gmres_stats* stats, void* stream);
+int gmres_solve_host(const gmres_csr* A_host, const double* b, double* x,
+                     const gmres_params* p, gmres_stats* stats, void* stream);
+
+/* ---- Plans: keep the workspace, the low-precision copy of A, the polynomial
+ * and the captured CUDA graph of one cycle between solves. ----------------- */
+typedef struct gmres_plan_s* gmres_plan;
+
+/* kind: 0 = FP64 GMRES, 1 = GMRES-IR with p->inner_prec.  A's arrays must stay
+ * valid until gmres_plan_destroy. */
+int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const gmres_params* p,
+                      void* stream);
+int gmres_plan_solve(gmres_plan plan, const double* b, double* x, gmres_stats* stats,
+                     void* stream);
+int gmres_plan_destroy(gmres_plan plan);
+
+/* ---- Building blocks on a plan (the hot-path kernels, exposed for tests) - */
+
+/* y = A v with the plan's inner copy of A: v is DEVICE, n doubles; it is
+ * scaled and rounded to the plan's storage precision exactly as a basis
+ * vector is; y is DEVICE, n values of the working type (double for FP64
+ * plans, float otherwise).  Runs the fused SpMV kernel of the Arnoldi step. */
+int gmres_plan_spmv(gmres_plan plan, const double* v, void* y, void* stream);
+
+/* Arnoldi with CGS2 from v0 (DEVICE, n doubles) for `steps` steps (<= m),
+ * the cycle kernels of the solver without the stopping test.  V_out: DEVICE,
+ * (steps+1) columns of n values in the storage type (double, float, half or
+ * bfloat16; FP16 values are scaled by sqrt(n)).  H_out: HOST, (steps+1) x
+ * steps FP64, column-major.  *k_out = steps taken (fewer after a breakdown). */
+int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V_out,
+                       double* H_out, int32_t* k_out, void* stream);
+
+/* GMRES-polynomial set-up (Section 3.4): `degree`+1 FP64 Arnoldi steps on
+ * the GPU from the SplitMix64 vector of `seed` (or from v0 if non-NULL,
+ * DEVICE, n doubles), harmonic Ritz values on the host, Leja ordering.
+ * roots_re/roots_im: HOST arrays of degree+1 entries; *nroots = roots
+ * written (fewer after an Arnoldi breakdown). */
+int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const double* v0,
+                     double* roots_re, double* roots_im, int32_t* nroots, void* stream);
+
+/* SplitMix64 vector on the device: out[i] in [-1, 1) (DEVICE, n doubles). */
+int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMRES_IR_H */

@@ -1,0 +1,305 @@
+"""Python binding of the B300 GMRES / GMRES-IR library (libgmres_ir.so).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Device memory comes from PyTorch tensors (their data pointers are
+passed through the C ABI declared in include/gmres_ir.h) and streams from
+torch.cuda.  There is no CPU fallback: if the shared library or a CUDA device
+is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgmres_ir.so")
+
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: "ERR_INVALID",
+          5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TOO_LARGE"}
+OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TOO_LARGE = range(8)
+MAX_RESTART = 512
+MAX_POLY_DEGREE = 96
+
+
+class GmresError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class csr_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+class params_t(ctypes.Structure):
+    _fields_ = [("restart_m", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("inner_rtol", ctypes.c_double), ("max_iters", ctypes.c_int64),
+                ("inner_prec", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32)]
+
+
+class stats_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int64),
+                ("outer_iters", ctypes.c_int32), ("rel_resid", ctypes.c_double),
+                ("t_solve_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("history_len", ctypes.c_int64), ("history", ctypes.c_void_p),
+                ("history_cap", ctypes.c_int64)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_SIGNATURES = {
+    "gmres_default_params": (None, [ctypes.POINTER(params_t)]),
+    "gmres_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmres_solve": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t),
+                                   ctypes.POINTER(stats_t), _P]),
+    "gmres_ir_solve": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t),
+                                      ctypes.POINTER(stats_t), _P]),
+    "gmres_solve_host": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t),
+                                        ctypes.POINTER(stats_t), _P]),
+    "gmres_ir_solve_host": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P,
+                                           ctypes.POINTER(params_t), ctypes.POINTER(stats_t), _P]),
+    "gmres_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(csr_t), _I32,
+                                         ctypes.POINTER(params_t), _P]),
+    "gmres_plan_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(stats_t), _P]),
+    "gmres_plan_destroy": (ctypes.c_int, [_P]),
+    "gmres_plan_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gmres_plan_arnoldi": (ctypes.c_int, [_P, _P, _I32, _P, _P, ctypes.POINTER(_I32), _P]),
+    "gmres_poly_roots": (ctypes.c_int, [ctypes.POINTER(csr_t), _I32, _U64, _P, _P, _P,
+                                        ctypes.POINTER(_I32), _P]),
+    "gmres_splitmix64_fill": (ctypes.c_int, [_P, _I64, _U64, _P]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgmres_ir.so (built in-tree by paper_2109_01232_b300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python paper_2109_01232_b300/build.py`")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the GMRES library needs a CUDA device (none is visible)")
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _check(code: int, what: str, allowed=(OK,)):
+    if code not in allowed:
+        raise GmresError(code, what)
+    return code
+
+
+def default_params(**kw) -> params_t:
+    p = params_t()
+    lib().gmres_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "inner_prec" and isinstance(v, str):
+            v = PREC[v]
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class DeviceCSR:
+    """CSR matrix on the device (int32 indices, FP64 values) backed by torch tensors."""
+
+    def __init__(self, row_ptr, col_idx, vals, n: int | None = None):
+        torch = _torch()
+        self.row_ptr = torch.as_tensor(row_ptr, dtype=torch.int32, device="cuda").contiguous()
+        self.col_idx = torch.as_tensor(col_idx, dtype=torch.int32, device="cuda").contiguous()
+        self.vals = torch.as_tensor(vals, dtype=torch.float64, device="cuda").contiguous()
+        self.n = int(n if n is not None else self.row_ptr.numel() - 1)
+        self.nnz = int(self.vals.numel())
+
+    @classmethod
+    def from_problem(cls, p) -> "DeviceCSR":
+        return cls(p.row_ptr, p.col_idx, p.vals, p.n)
+
+    def c(self) -> csr_t:
+        return csr_t(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.vals))
+
+
+@dataclass
+class SolveResult:
+    status: int
+    iters: int
+    outer: int
+    relres: float
+    t_solve_ms: float
+    t_setup_ms: float
+    history: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def status_name(self) -> str:
+        return STATUS[self.status]
+
+
+def _result(code: int, st: stats_t, hist: np.ndarray | None) -> SolveResult:
+    _check(code, "solve", (OK, NOT_CONVERGED, BREAKDOWN, NONFINITE))
+    h = hist[:st.history_len].copy() if hist is not None else np.zeros(0)
+    return SolveResult(code, int(st.iters), int(st.outer_iters), float(st.rel_resid),
+                       float(st.t_solve_ms), float(st.t_setup_ms), h)
+
+
+def _stats(params: params_t):
+    st = stats_t()
+    hist = None
+    if params.record_history:
+        hist = np.zeros(max(int(params.max_iters), 1), dtype=np.float64)
+        st.history = hist.ctypes.data
+        st.history_cap = hist.size
+    return st, hist
+
+
+def _solve(fn_name: str, A: DeviceCSR, b, x, stream=None, **kw) -> SolveResult:
+    p = default_params(**kw)
+    st, hist = _stats(p)
+    c = A.c()
+    code = getattr(lib(), fn_name)(ctypes.byref(c), _ptr(b), _ptr(x), ctypes.byref(p),
+                                   ctypes.byref(st), _stream(stream))
+    return _result(code, st, hist)
+
+
+def gmres_solve(A: DeviceCSR, b, x, stream=None, **kw) -> SolveResult:
+    """FP64 GMRES(m) (Algorithm 1, CGS2).  b, x: float64 CUDA tensors; x is updated."""
+    return _solve("gmres_solve", A, b, x, stream, **kw)
+
+
+def gmres_ir_solve(A: DeviceCSR, b, x, stream=None, **kw) -> SolveResult:
+    """GMRES-IR (Algorithm 2) with inner precision kw['inner_prec'] ('fp32' default)."""
+    return _solve("gmres_ir_solve", A, b, x, stream, **kw)
+
+
+def _solve_host(fn_name, row_ptr, col_idx, vals, b, x, stream=None, **kw) -> SolveResult:
+    """Host-memory variant: numpy (or pinned torch CPU) arrays; x is updated in place."""
+    p = default_params(**kw)
+    st, hist = _stats(p)
+    arrs = [np.ascontiguousarray(row_ptr, np.int32), np.ascontiguousarray(col_idx, np.int32),
+            np.ascontiguousarray(vals, np.float64)]
+    c = csr_t(len(arrs[0]) - 1, len(arrs[2]), arrs[0].ctypes.data, arrs[1].ctypes.data,
+              arrs[2].ctypes.data)
+    bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
+    xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    code = getattr(lib(), fn_name)(ctypes.byref(c), bp, xp, ctypes.byref(p), ctypes.byref(st),
+                                   _stream(stream))
+    return _result(code, st, hist)
+
+
+def gmres_ir_solve_host(row_ptr, col_idx, vals, b, x, stream=None, **kw) -> SolveResult:
+    return _solve_host("gmres_ir_solve_host", row_ptr, col_idx, vals, b, x, stream, **kw)
+
+
+def gmres_solve_host(row_ptr, col_idx, vals, b, x, stream=None, **kw) -> SolveResult:
+    return _solve_host("gmres_solve_host", row_ptr, col_idx, vals, b, x, stream, **kw)
+
+
+class Plan:
+    """Reusable solver workspace + captured cycle graph for one matrix.
+
+    kind: 'gmres' (FP64 GMRES) or 'ir' (GMRES-IR with inner_prec)."""
+
+    def __init__(self, A: DeviceCSR, kind: str = "ir", stream=None, **kw):
+        self.A = A
+        self.params = default_params(**kw)
+        self.kind = {"gmres": 0, "ir": 1}[kind]
+        self.prec = 0 if self.kind == 0 else self.params.inner_prec
+        h = ctypes.c_void_p()
+        c = A.c()
+        _check(lib().gmres_plan_create(ctypes.byref(h), ctypes.byref(c), self.kind,
+                                       ctypes.byref(self.params), _stream(stream)), "plan_create")
+        self.handle = h
+
+    @property
+    def storage_dtype(self):
+        torch = _torch()
+        return {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}[self.prec]
+
+    @property
+    def work_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.prec == 0 else torch.float32
+
+    def solve(self, b, x, stream=None) -> SolveResult:
+        st, hist = _stats(self.params)
+        code = lib().gmres_plan_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(st),
+                                      _stream(stream))
+        return _result(code, st, hist)
+
+    def spmv(self, v, stream=None):
+        torch = _torch()
+        y = torch.empty(self.A.n, dtype=self.work_dtype, device="cuda")
+        _check(lib().gmres_plan_spmv(self.handle, _ptr(v), _ptr(y), _stream(stream)), "spmv")
+        return y
+
+    def arnoldi(self, v0, steps: int, stream=None):
+        """Returns (V (steps+1, n) tensor in the storage dtype, H numpy (steps+1, steps), k)."""
+        torch = _torch()
+        V = torch.zeros((steps + 1, self.A.n), dtype=self.storage_dtype, device="cuda")
+        H = np.zeros((steps, steps + 1), dtype=np.float64)  # column-major (steps+1) x steps
+        k = ctypes.c_int32(0)
+        _check(lib().gmres_plan_arnoldi(self.handle, _ptr(v0), steps, _ptr(V), H.ctypes.data,
+                                        ctypes.byref(k), _stream(stream)), "arnoldi")
+        return V, H.T.copy(), int(k.value)
+
+    def close(self):
+        if self.handle:
+            lib().gmres_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def poly_roots(A: DeviceCSR, degree: int, seed: int = 0, v0=None, stream=None) -> np.ndarray:
+    """Leja-ordered roots of the GMRES polynomial of the given degree (complex numpy array)."""
+    re = np.zeros(degree + 1)
+    im = np.zeros(degree + 1)
+    nr = ctypes.c_int32(0)
+    c = A.c()
+    _check(lib().gmres_poly_roots(ctypes.byref(c), degree, seed, _ptr(v0) if v0 is not None else None,
+                                  re.ctypes.data, im.ctypes.data, ctypes.byref(nr),
+                                  _stream(stream)), "poly_roots")
+    return re[:nr.value] + 1j * im[:nr.value]
+
+
+def splitmix64(n: int, seed: int, stream=None):
+    """SplitMix64 vector in [-1, 1) computed on the device."""
+    torch = _torch()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(lib().gmres_splitmix64_fill(_ptr(out), n, seed, _stream(stream)), "splitmix64")
+    return out

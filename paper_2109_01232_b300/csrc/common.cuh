@@ -1,0 +1,128 @@
+// common.cuh -- precision traits, vector memory helpers, warp reductions and the
+// device-resident solver state shared by the GMRES kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace gm {
+
+constexpr int NT = 256;           // threads per CTA of the streaming kernels
+constexpr int NWARP = NT / 32;
+constexpr int LSQ_MAX = 512;      // largest restart length (GMRES_MAX_RESTART)
+constexpr int TILE_MAX = 2048;    // largest SpMV row tile; every buffer's leading dimension
+                                  // is a multiple of it, so tiles never cross the padding
+
+// Precision of the inner cycle: S = storage type of the Krylov basis and of the
+// copy of A, W = working (accumulation) type, VEC = rows per 16-byte vector of S.
+template <int P> struct Tr;
+template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2; };
+template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4; };
+template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8; };
+template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8; };
+
+// storage -> working type
+__device__ __forceinline__ double to_w(double v) { return v; }
+__device__ __forceinline__ float to_w(float v) { return v; }
+__device__ __forceinline__ float to_w(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_w(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// round to the storage type (round to nearest even)
+template <class S> __device__ __forceinline__ S to_s(double v);
+template <class S> __device__ __forceinline__ S to_s(float v);
+template <> __device__ __forceinline__ double to_s<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_s<double>(float v) { return (double)v; }
+template <> __device__ __forceinline__ float to_s<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ float to_s<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_s<__half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ __half to_s<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// N consecutive elements through 16-byte loads/stores (p must be 16-byte aligned).
+template <class T, int N>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T (&o)[N]) {
+  static_assert((sizeof(T) * N) % 16 == 0, "vector must be a multiple of 16 bytes");
+  constexpr int Q = (int)(sizeof(T) * N / 16);
+  uint4 u[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) u[q] = reinterpret_cast<const uint4*>(p)[q];
+  memcpy(o, u, sizeof(u));
+}
+template <class T, int N>
+__device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[N]) {
+  constexpr int Q = (int)(sizeof(T) * N / 16);
+  uint4 u[Q];
+  memcpy(u, o, sizeof(u));
+#pragma unroll
+  for (int q = 0; q < Q; ++q) reinterpret_cast<uint4*>(p)[q] = u[q];
+}
+// Streaming load of data that is read once per kernel (evict-first in L1/L2).
+template <class T, int N>
+__device__ __forceinline__ void ldv_stream(const T* __restrict__ p, T (&o)[N]) {
+  constexpr int Q = (int)(sizeof(T) * N / 16);
+  uint4 u[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) u[q] = __ldcs(reinterpret_cast<const uint4*>(p) + q);
+  memcpy(o, u, sizeof(u));
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Status codes (mirrors gmres_status in include/gmres_ir.h).
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3, ST_INVALID = 4 };
+
+// Device-resident state of one solve.  The host writes it once before a solve and
+// reads it once after; every decision in between is taken on the device.
+struct DevState {
+  int stop;          // 1: the solve is finished (status holds why)
+  int cycle_done;    // 1: the current Arnoldi cycle has ended
+  int status;
+  int k;             // Arnoldi steps taken in the current cycle
+  int k_used;        // columns used by the least-squares solve (after trimming)
+  int singular;      // 1: the last least-squares factor was singular
+  int breakdown;     // 1: the last cycle ended by a (lucky) breakdown
+  int outer;         // cycles completed
+  int m;             // restart length
+  int mode;          // 0: FP64 GMRES (implicit test against rtol), 1: IR (inner_rtol)
+  int zero_rhs;      // 1: ||b|| = 0, the answer is x = 0
+  int hist_cap;      // capacity of the residual history
+  long long iters;   // Arnoldi steps over the whole solve
+  long long max_iters;
+  double rtol, inner_rtol;
+  double bnorm, gamma, relres;
+  double stop_rel;   // implicit-residual threshold of the current cycle, relative to gamma
+  double sigma;      // 1 / norm of the next SpMV source vector
+  double wnorm;      // ||A v_j|| of the current step (breakdown test)
+  double u_work;     // unit roundoff of the working precision
+  unsigned int ticket[4];
+};
+
+// Small dense arrays of the cycle (FP64, device memory, one allocation).
+struct Arrays {
+  double* h1;    // m+2   first CGS pass coefficients (plus spare)
+  double* h2;    // m+2   second CGS pass coefficients
+  double* H;     // (m+1) x m, column-major, unrotated Hessenberg matrix
+  double* R;     // (m+1) x m, column-major, after the Givens rotations
+  double* cs;    // m
+  double* sn;    // m
+  double* g;     // m+1   rotated right-hand side (g[0] = 1 at a cycle start)
+  double* y;     // m     least-squares solution
+  double* hist;  // hist_cap relative residual estimates
+};
+
+}  // namespace gm

@@ -1,0 +1,670 @@
+// solver.cu -- plans, CUDA-graph capture of one restart cycle, and the C ABI.
+//
+// A plan owns the workspace of one matrix: the Krylov basis V ((m+1) columns of
+// ld values in the storage precision), three work vectors, the FP64 residual /
+// iterate / right-hand-side buffers, the low-precision copy of A, the Hessenberg
+// arrays and the device state.  One restart cycle of Algorithm 1 / Algorithm 2
+// (m Arnoldi steps, least squares, x update, FP64 residual) is captured once as
+// a CUDA graph; a solve launches that graph until the device state says stop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gmres_ir.h"
+#include "kernels.cuh"
+#include "poly_host.h"
+
+namespace gm {
+
+static int map_err(cudaError_t e) {
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
+}
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return map_err(e_);    \
+  } while (0)
+
+static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+struct Plan {
+  int kind = 1;  // 0: FP64 GMRES, 1: GMRES-IR
+  int prec = 1;  // storage precision of the cycle
+  gmres_csr A{};
+  int n = 0, m = 0;
+  long long ld = 0;
+  gmres_params p{};
+  double a_scale = 1.0, v_scale = 1.0;
+  void* aval = nullptr;  // low-precision copy of A's values (A.vals itself for FP64)
+  bool own_aval = false;
+  void* V = nullptr;
+  void *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;
+  double *r = nullptr, *xb = nullptr, *bb = nullptr;
+  void* part = nullptr;
+  DevState* st = nullptr;
+  DevState* h_st = nullptr;  // pinned
+  double* arr_mem = nullptr;
+  Arrays arr{};
+  int hist_cap = 0;
+  int sms = 148;
+  int grid_spmv = 1, grid_vec = 1, grid_res = 1;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // polynomial preconditioner (right, p(A) in product form)
+  std::vector<double> roots_re, roots_im;
+  double t_setup_ms = 0.0;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launch sequences (templated on the storage precision).
+// ---------------------------------------------------------------------------
+template <int P>
+static void launch_step(Plan& pl, int j, cudaStream_t s) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  S* V = (S*)pl.V;
+  W* w1 = (W*)pl.w1;
+  W* w2 = (W*)pl.w2;
+  W* w3 = (W*)pl.w3;
+  W* part = (W*)pl.part;
+  const double rs = pl.a_scale / pl.v_scale;
+  const size_t sm1 = SpmvSmem<P>::bytes(j + 2);
+  if (j == 0)
+    k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, sm1, s>>>(
+        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, pl.r, pl.v_scale, V, 0,
+        w1, part, pl.st, pl.arr.h1);
+  else
+    k_spmv_arnoldi<P, W><<<pl.grid_spmv, NT, sm1, s>>>(
+        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, w3, pl.v_scale, V, j, w1,
+        part, pl.st, pl.arr.h1);
+  k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
+      V, pl.ld, j, pl.v_scale, w1, w2, part, pl.st, pl.arr.h1, pl.arr.h2);
+  k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1), s>>>(V, pl.ld, j, pl.v_scale, w2, w3,
+                                                                   part, pl.st, pl.arr);
+}
+
+static void launch_residual(Plan& pl, int first, cudaStream_t s) {
+  k_residual<<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals, pl.n,
+                                                       pl.xb, pl.bb, pl.r, (double*)pl.part, pl.st,
+                                                       pl.arr, first);
+}
+
+template <int P>
+static void launch_cycle_tail(Plan& pl, cudaStream_t s) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  k_lsq<<<1, 32, 0, s>>>(pl.st, pl.arr);
+  k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
+                                                             pl.st, pl.arr.y, pl.xb);
+  launch_residual(pl, 0, s);
+}
+
+template <int P>
+static void launch_cycle(Plan& pl, cudaStream_t s) {
+  for (int j = 0; j < pl.m; ++j) launch_step<P>(pl, j, s);
+  launch_cycle_tail<P>(pl, s);
+}
+
+template <int P>
+static int configure(Plan& pl) {
+  using W = typename Tr<P>::W;
+  constexpr int VEC = Tr<P>::VEC;
+  const size_t sm_max = SpmvSmem<P>::bytes(pl.m + 2);
+  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_max));
+  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_max));
+  const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
+  CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_u1));
+  int occ = 1;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_arnoldi<P, W>, NT, sm_max));
+  const long long ntiles = (pl.n + SpmvSmem<P>::TR - 1) / SpmvSmem<P>::TR;
+  pl.grid_spmv = (int)std::max(1LL, std::min(ntiles, (long long)std::max(occ, 1) * pl.sms));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_u1<P>, NT, sm_u1));
+  const long long nblk = pl.ld / ((long long)NT * VEC);
+  pl.grid_vec = (int)std::max(1LL, std::min(nblk, (long long)std::max(occ, 1) * pl.sms));
+  return GMRES_OK;
+}
+
+static int configure_residual(Plan& pl) {
+  int occ = 1;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual, NT, residual_smem()));
+  const long long ntiles = (pl.n + RES_TR - 1) / RES_TR;
+  pl.grid_res = (int)std::max(1LL, std::min(ntiles, (long long)std::max(occ, 1) * pl.sms));
+  return GMRES_OK;
+}
+
+template <class F>
+static int dispatch(int prec, F&& f) {
+  switch (prec) {
+    case GMRES_FP64: return f(std::integral_constant<int, 0>{});
+    case GMRES_FP32: return f(std::integral_constant<int, 1>{});
+    case GMRES_FP16: return f(std::integral_constant<int, 2>{});
+    case GMRES_BF16: return f(std::integral_constant<int, 3>{});
+  }
+  return GMRES_ERR_INVALID;
+}
+
+static size_t storage_bytes(int prec) { return prec == 0 ? 8 : prec == 1 ? 4 : 2; }
+static size_t work_bytes(int prec) { return prec == 0 ? 8 : 4; }
+
+static void plan_free(Plan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
+  if (pl->ev0) cudaEventDestroy(pl->ev0);
+  if (pl->ev1) cudaEventDestroy(pl->ev1);
+  if (pl->own_aval) cudaFree(pl->aval);
+  cudaFree(pl->V);
+  cudaFree(pl->w1);
+  cudaFree(pl->w2);
+  cudaFree(pl->w3);
+  cudaFree(pl->r);
+  cudaFree(pl->xb);
+  cudaFree(pl->bb);
+  cudaFree(pl->part);
+  cudaFree(pl->st);
+  cudaFree(pl->arr_mem);
+  if (pl->h_st) cudaFreeHost(pl->h_st);
+  delete pl;
+}
+
+static int validate_csr(const gmres_csr* A) {
+  if (!A || A->n < 0 || A->nnz < 0) return GMRES_ERR_INVALID;
+  if (A->n > 0 && (!A->row_ptr || !A->vals || (A->nnz > 0 && !A->col_idx))) return GMRES_ERR_INVALID;
+  return GMRES_OK;
+}
+
+static int validate_params(const gmres_params* p) {
+  if (!p) return GMRES_ERR_INVALID;
+  if (p->restart_m < 1) return GMRES_ERR_INVALID;
+  if (p->restart_m > GMRES_MAX_RESTART) return GMRES_ERR_TOO_LARGE;
+  if (!(p->rtol >= 0.0) || !(p->inner_rtol >= 0.0) || p->max_iters < 0) return GMRES_ERR_INVALID;
+  if (p->inner_prec < 0 || p->inner_prec > 3) return GMRES_ERR_INVALID;
+  if (p->poly_degree < 0) return GMRES_ERR_INVALID;
+  if (p->poly_degree > GMRES_MAX_POLY_DEGREE) return GMRES_ERR_TOO_LARGE;
+  return GMRES_OK;
+}
+
+// Device check of the CSR structure (once per plan).
+static int check_csr_device(const gmres_csr* A, cudaStream_t s) {
+  int* d_bad = nullptr;
+  CK(cudaMallocAsync((void**)&d_bad, sizeof(int), s));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+  k_check_csr<<<256, 256, 0, s>>>(A->row_ptr, A->col_idx, A->n, A->nnz, d_bad);
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaFreeAsync(d_bad, s));
+  CK(cudaStreamSynchronize(s));
+  return bad ? GMRES_ERR_INVALID : GMRES_OK;
+}
+
+int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p, cudaStream_t s) {
+  *out = nullptr;
+  if (int e = validate_csr(A)) return e;
+  if (int e = validate_params(p)) return e;
+  if (kind != 0 && kind != 1) return GMRES_ERR_INVALID;
+  if (A->n == 0) return GMRES_ERR_INVALID;  // an empty system has no plan (solves return OK)
+  Plan* pl = new (std::nothrow) Plan();
+  if (!pl) return GMRES_ERR_OOM;
+  auto fail = [&](int e) {
+    cudaStreamSynchronize(s);
+    plan_free(pl);
+    return e;
+  };
+  pl->kind = kind;
+  pl->prec = kind == 0 ? GMRES_FP64 : p->inner_prec;
+  pl->A = *A;
+  pl->n = A->n;
+  pl->m = p->restart_m;
+  pl->p = *p;
+  pl->ld = round_up(std::max(A->n, 1), TILE_MAX);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (int e = check_csr_device(A, s)) return fail(e);
+
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, s);
+  const size_t sb = storage_bytes(pl->prec), wb = work_bytes(pl->prec);
+  const long long ld = pl->ld, m = pl->m;
+  auto alloc = [&](void** ptr, size_t bytes) -> int {
+    if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return map_err(cudaErrorMemoryAllocation);
+    if (cudaMemsetAsync(*ptr, 0, std::max<size_t>(bytes, 16), s) != cudaSuccess) return GMRES_ERR_CUDA;
+    return GMRES_OK;
+  };
+  int e = GMRES_OK;
+  if ((e = alloc(&pl->V, sb * (size_t)ld * (m + 1)))) return fail(e);
+  if ((e = alloc(&pl->w1, wb * (size_t)ld))) return fail(e);
+  if ((e = alloc(&pl->w2, wb * (size_t)ld))) return fail(e);
+  if ((e = alloc(&pl->w3, wb * (size_t)ld))) return fail(e);
+  if ((e = alloc((void**)&pl->r, 8 * (size_t)ld))) return fail(e);
+  if ((e = alloc((void**)&pl->xb, 8 * (size_t)ld))) return fail(e);
+  if ((e = alloc((void**)&pl->bb, 8 * (size_t)ld))) return fail(e);
+  if ((e = alloc((void**)&pl->st, sizeof(DevState)))) return fail(e);
+  pl->hist_cap = p->record_history ? (int)std::min<int64_t>(std::max<int64_t>(p->max_iters, 1), 1 << 22) : 1;
+  const size_t arr_n = 2 * (m + 2) + 2 * (m + 1) * m + 2 * m + (m + 1) + m + pl->hist_cap;
+  if ((e = alloc((void**)&pl->arr_mem, 8 * arr_n))) return fail(e);
+  double* q = pl->arr_mem;
+  pl->arr.h1 = q; q += m + 2;
+  pl->arr.h2 = q; q += m + 2;
+  pl->arr.H = q; q += (m + 1) * m;
+  pl->arr.R = q; q += (m + 1) * m;
+  pl->arr.cs = q; q += m;
+  pl->arr.sn = q; q += m;
+  pl->arr.g = q; q += m + 1;
+  pl->arr.y = q; q += m;
+  pl->arr.hist = q;
+  if (cudaMallocHost((void**)&pl->h_st, sizeof(DevState)) != cudaSuccess) return fail(GMRES_ERR_OOM);
+
+  // Low-precision copy of A: values / s_A rounded to the storage type.
+  if (pl->prec == GMRES_FP64) {
+    pl->aval = (void*)A->vals;
+  } else {
+    if (pl->prec == GMRES_FP16 && A->nnz > 0) {
+      unsigned long long* d_mx = nullptr;
+      if (cudaMalloc((void**)&d_mx, 8) != cudaSuccess) return fail(GMRES_ERR_OOM);
+      cudaMemsetAsync(d_mx, 0, 8, s);
+      k_absmax<<<pl->sms * 4, 256, 0, s>>>(A->vals, A->nnz, d_mx);
+      unsigned long long bits = 0;
+      cudaMemcpyAsync(&bits, d_mx, 8, cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) { cudaFree(d_mx); return fail(GMRES_ERR_CUDA); }
+      cudaFree(d_mx);
+      double mx;
+      memcpy(&mx, &bits, 8);
+      if (!std::isfinite(mx)) return fail(GMRES_NONFINITE);
+      pl->a_scale = mx > 0.0 ? mx : 1.0;
+      pl->v_scale = std::sqrt((double)pl->n);
+    }
+    if ((e = alloc(&pl->aval, sb * (size_t)std::max(A->nnz, 1)))) return fail(e);
+    pl->own_aval = true;
+    const int blocks = pl->sms * 8;
+    if (pl->prec == GMRES_FP32)
+      k_cast_vals<float><<<blocks, 256, 0, s>>>(A->vals, (float*)pl->aval, A->nnz, pl->a_scale);
+    else if (pl->prec == GMRES_FP16)
+      k_cast_vals<__half><<<blocks, 256, 0, s>>>(A->vals, (__half*)pl->aval, A->nnz, pl->a_scale);
+    else
+      k_cast_vals<__nv_bfloat16><<<blocks, 256, 0, s>>>(A->vals, (__nv_bfloat16*)pl->aval, A->nnz,
+                                                        pl->a_scale);
+  }
+  if ((e = dispatch(pl->prec, [&](auto P) { return configure<decltype(P)::value>(*pl); }))) return fail(e);
+  if ((e = configure_residual(*pl))) return fail(e);
+  const int gmax = std::max({pl->grid_spmv, pl->grid_vec, pl->grid_res});
+  if ((e = alloc(&pl->part, 8 * (size_t)(m + 2) * gmax))) return fail(e);
+  cudaEventRecord(t1, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, t0, t1);
+  pl->t_setup_ms = ms;
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+
+  // Polynomial preconditioner roots (set-up, FP64 Arnoldi on the GPU + host eigenvalues).
+  if (p->poly_degree > 0) return fail(GMRES_ERR_INVALID);  // applied in the cycle: not built yet
+  if (p->poly_degree > 0) {
+    std::vector<double> re(p->poly_degree + 1), im(p->poly_degree + 1);
+    int nr = 0;
+    auto tp0 = std::chrono::steady_clock::now();
+    e = gmres_poly_roots(A, p->poly_degree, p->seed, nullptr, re.data(), im.data(), &nr, s);
+    if (e) return fail(e);
+    pl->roots_re.assign(re.begin(), re.begin() + nr);
+    pl->roots_im.assign(im.begin(), im.begin() + nr);
+    pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
+  }
+
+  // Capture one restart cycle as a CUDA graph.
+  if (cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  if (cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess)
+    return fail(GMRES_ERR_CUDA);
+  if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(GMRES_ERR_CUDA);
+  dispatch(pl->prec, [&](auto P) {
+    launch_cycle<decltype(P)::value>(*pl, pl->cap);
+    return 0;
+  });
+  if (cudaStreamEndCapture(pl->cap, &pl->graph) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  if (cudaGraphInstantiate(&pl->exec, pl->graph, 0) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  *out = pl;
+  return GMRES_OK;
+}
+
+static void init_state(Plan& pl, DevState& h) {
+  memset(&h, 0, sizeof(h));
+  h.m = pl.m;
+  h.mode = pl.kind == 0 ? 0 : 1;
+  h.max_iters = pl.p.max_iters;
+  h.rtol = pl.p.rtol;
+  h.inner_rtol = pl.p.inner_rtol;
+  h.u_work = pl.prec == GMRES_FP64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  h.hist_cap = pl.hist_cap;
+  h.sigma = 1.0;
+}
+
+int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStream_t s) {
+  if (!b || !x) return GMRES_ERR_INVALID;
+  const size_t nb = sizeof(double) * (size_t)pl.n;
+  init_state(pl, *pl.h_st);
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(pl.bb, b, nb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(pl.xb, x, nb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaEventRecord(pl.ev0, s));
+  launch_residual(pl, 1, s);
+  CK(cudaGetLastError());
+  int* h_stop = &pl.h_st->stop;
+  CK(cudaMemcpyAsync(h_stop, &pl.st->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const long long max_cycles = pl.p.max_iters + 2;
+  for (long long c = 0; !*h_stop && c < max_cycles; ++c) {
+    CK(cudaGraphLaunch(pl.exec, s));
+    CK(cudaMemcpyAsync(h_stop, &pl.st->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaEventRecord(pl.ev1, s));
+  CK(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const DevState& h = *pl.h_st;
+  if (h.zero_rhs) CK(cudaMemsetAsync(x, 0, nb, s));
+  else CK(cudaMemcpyAsync(x, pl.xb, nb, cudaMemcpyDeviceToDevice, s));
+  if (stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pl.ev0, pl.ev1);
+    stats->status = h.status;
+    stats->iters = h.iters;
+    stats->outer_iters = h.outer;
+    stats->rel_resid = h.relres;
+    stats->t_solve_ms = ms;
+    stats->t_setup_ms = pl.t_setup_ms;
+    stats->history_len = 0;
+    if (stats->history && stats->history_cap > 0 && pl.p.record_history) {
+      const long long cnt = std::min<long long>({(long long)h.iters, (long long)pl.hist_cap, stats->history_cap});
+      if (cnt > 0)
+        CK(cudaMemcpyAsync(stats->history, pl.arr.hist, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+      stats->history_len = cnt;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  return h.status;
+}
+
+// ---------------------------------------------------------------------------
+// Test entry points on a plan.
+// ---------------------------------------------------------------------------
+int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
+  init_state(pl, *pl.h_st);
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  int e = dispatch(pl.prec, [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    using S = typename Tr<P>::S;
+    using W = typename Tr<P>::W;
+    k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, SpmvSmem<P>::bytes(2), s>>>(
+        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, pl.a_scale / pl.v_scale, v,
+        pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, (W*)pl.part, pl.st, pl.arr.h1);
+    return (int)cudaMemcpyAsync(y, pl.w1, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
+  });
+  if (e) return GMRES_ERR_CUDA;
+  CK(cudaStreamSynchronize(s));
+  return GMRES_OK;
+}
+
+int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_out, int* k_out,
+                 cudaStream_t s) {
+  if (steps < 1 || steps > pl.m || !v0 || !H_out || !k_out) return GMRES_ERR_INVALID;
+  init_state(pl, *pl.h_st);
+  pl.h_st->mode = 1;
+  pl.h_st->rtol = 0.0;
+  pl.h_st->inner_rtol = 0.0;
+  pl.h_st->max_iters = 1LL << 62;
+  const size_t nb = sizeof(double) * (size_t)pl.n;
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(pl.bb, v0, nb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(pl.xb, 0, nb, s));
+  launch_residual(pl, 1, s);  // r = v0, sigma = 1/||v0||, g[0] = 1
+  int e = dispatch(pl.prec, [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    using S = typename Tr<P>::S;
+    using W = typename Tr<P>::W;
+    for (int j = 0; j < steps; ++j) launch_step<P>(pl, j, s);
+    k_store_basis<P, W><<<pl.sms * 4, 256, 0, s>>>((const W*)pl.w3, pl.v_scale, pl.n, (S*)pl.V, pl.ld,
+                                                   steps, pl.st);
+    return (int)cudaGetLastError();
+  });
+  if (e) return GMRES_ERR_CUDA;
+  CK(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int k = pl.h_st->k;
+  *k_out = k;
+  const size_t sb = storage_bytes(pl.prec);
+  if (V_out)
+    CK(cudaMemcpy2DAsync(V_out, sb * pl.n, pl.V, sb * pl.ld, sb * pl.n, steps + 1, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> Hfull((size_t)(pl.m + 1) * pl.m);
+  CK(cudaMemcpyAsync(Hfull.data(), pl.arr.H, sizeof(double) * Hfull.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int c = 0; c < steps; ++c)
+    for (int i = 0; i <= steps; ++i)
+      H_out[i + (size_t)c * (steps + 1)] = (c < k && i <= c + 1) ? Hfull[i + (size_t)c * (pl.m + 1)] : 0.0;
+  return pl.h_st->status == ST_NONFINITE ? GMRES_NONFINITE : GMRES_OK;
+}
+
+}  // namespace gm
+
+using gm::Plan;
+
+struct gmres_plan_s {
+  Plan* pl;
+};
+
+extern "C" {
+
+void gmres_default_params(gmres_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->restart_m = 50;
+  p->rtol = 1e-10;
+  p->inner_rtol = 0.0;
+  p->max_iters = 100000;
+  p->inner_prec = GMRES_FP32;
+  p->poly_degree = 0;
+  p->seed = 0;
+  p->record_history = 0;
+}
+
+const char* gmres_status_string(int status) {
+  switch (status) {
+    case GMRES_OK: return "converged";
+    case GMRES_NOT_CONVERGED: return "maximum iterations reached";
+    case GMRES_BREAKDOWN: return "breakdown: singular least-squares factor";
+    case GMRES_NONFINITE: return "non-finite value in the input or a reduction";
+    case GMRES_ERR_INVALID: return "invalid argument";
+    case GMRES_ERR_OOM: return "device allocation failed";
+    case GMRES_ERR_CUDA: return "CUDA runtime error";
+    case GMRES_ERR_TOO_LARGE: return "size exceeds a documented maximum";
+  }
+  return "unknown status";
+}
+
+int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const gmres_params* p,
+                      void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  *plan = nullptr;
+  Plan* pl = nullptr;
+  int e = gm::plan_create(&pl, A, kind, p, (cudaStream_t)stream);
+  if (e) return e;
+  auto* h = new (std::nothrow) gmres_plan_s{pl};
+  if (!h) {
+    gm::plan_free(pl);
+    return GMRES_ERR_OOM;
+  }
+  *plan = h;
+  return GMRES_OK;
+}
+
+int gmres_plan_destroy(gmres_plan plan) {
+  if (!plan) return GMRES_ERR_INVALID;
+  cudaDeviceSynchronize();
+  gm::plan_free(plan->pl);
+  delete plan;
+  return GMRES_OK;
+}
+
+int gmres_plan_solve(gmres_plan plan, const double* b, double* x, gmres_stats* stats, void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  return gm::plan_solve(*plan->pl, b, x, stats, (cudaStream_t)stream);
+}
+
+int gmres_plan_spmv(gmres_plan plan, const double* v, void* y, void* stream) {
+  if (!plan || !v || !y) return GMRES_ERR_INVALID;
+  return gm::plan_spmv(*plan->pl, v, y, (cudaStream_t)stream);
+}
+
+int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V_out, double* H_out,
+                       int32_t* k_out, void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  return gm::plan_arnoldi(*plan->pl, v0, steps, V_out, H_out, k_out, (cudaStream_t)stream);
+}
+
+static int solve_once(const gmres_csr* A, const double* b, double* x, const gmres_params* p, int kind,
+                      gmres_stats* stats, void* stream) {
+  if (int e = gm::validate_csr(A)) return e;
+  if (int e = gm::validate_params(p)) return e;
+  if (!b || !x) return GMRES_ERR_INVALID;
+  if (A->n == 0) {
+    if (stats) {  // an empty system is solved by the empty vector
+      stats->status = GMRES_OK;
+      stats->iters = 0;
+      stats->outer_iters = 0;
+      stats->rel_resid = 0.0;
+      stats->t_solve_ms = stats->t_setup_ms = 0.0;
+      stats->history_len = 0;
+    }
+    return GMRES_OK;
+  }
+  Plan* pl = nullptr;
+  int e = gm::plan_create(&pl, A, kind, p, (cudaStream_t)stream);
+  if (e) {
+    if (stats) stats->status = e;
+    return e;
+  }
+  e = gm::plan_solve(*pl, b, x, stats, (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  gm::plan_free(pl);
+  return e;
+}
+
+int gmres_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                gmres_stats* stats, void* stream) {
+  return solve_once(A, b, x, p, 0, stats, stream);
+}
+
+int gmres_ir_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                   gmres_stats* stats, void* stream) {
+  return solve_once(A, b, x, p, 1, stats, stream);
+}
+
+static int solve_host(const gmres_csr* Ah, const double* b, double* x, const gmres_params* p, int kind,
+                      gmres_stats* stats, void* stream) {
+  if (int e = gm::validate_csr(Ah)) return e;
+  if (!b || !x) return GMRES_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)Ah->n, nnz = (size_t)Ah->nnz;
+  if (n == 0) return solve_once(Ah, b, x, p, kind, stats, stream);
+  int32_t *rp = nullptr, *ci = nullptr;
+  double *va = nullptr, *bd = nullptr, *xd = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(s);
+    cudaFree(rp); cudaFree(ci); cudaFree(va); cudaFree(bd); cudaFree(xd);
+  };
+  if (cudaMalloc((void**)&rp, 4 * (n + 1)) != cudaSuccess || cudaMalloc((void**)&ci, 4 * std::max<size_t>(nnz, 1)) != cudaSuccess ||
+      cudaMalloc((void**)&va, 8 * std::max<size_t>(nnz, 1)) != cudaSuccess || cudaMalloc((void**)&bd, 8 * n) != cudaSuccess ||
+      cudaMalloc((void**)&xd, 8 * n) != cudaSuccess) {
+    cleanup();
+    return GMRES_ERR_OOM;
+  }
+  cudaMemcpyAsync(rp, Ah->row_ptr, 4 * (n + 1), cudaMemcpyHostToDevice, s);
+  if (nnz) {
+    cudaMemcpyAsync(ci, Ah->col_idx, 4 * nnz, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(va, Ah->vals, 8 * nnz, cudaMemcpyHostToDevice, s);
+  }
+  cudaMemcpyAsync(bd, b, 8 * n, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(xd, x, 8 * n, cudaMemcpyHostToDevice, s);
+  gmres_csr Ad{Ah->n, Ah->nnz, rp, ci, va};
+  int e = solve_once(&Ad, bd, xd, p, kind, stats, stream);
+  if (e == GMRES_OK || e == GMRES_NOT_CONVERGED || e == GMRES_BREAKDOWN)
+    cudaMemcpyAsync(x, xd, 8 * n, cudaMemcpyDeviceToHost, s);
+  cleanup();
+  return e;
+}
+
+int gmres_ir_solve_host(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                        gmres_stats* stats, void* stream) {
+  return solve_host(A, b, x, p, 1, stats, stream);
+}
+
+int gmres_solve_host(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                     gmres_stats* stats, void* stream) {
+  return solve_host(A, b, x, p, 0, stats, stream);
+}
+
+int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const double* v0,
+                     double* roots_re, double* roots_im, int32_t* nroots, void* stream) {
+  if (int e = gm::validate_csr(A)) return e;
+  if (!roots_re || !roots_im || !nroots || degree < 1 || A->n < 1) return GMRES_ERR_INVALID;
+  if (degree > GMRES_MAX_POLY_DEGREE) return GMRES_ERR_TOO_LARGE;
+  cudaStream_t s = (cudaStream_t)stream;
+  gmres_params p;
+  gmres_default_params(&p);
+  p.restart_m = degree + 1;
+  Plan* pl = nullptr;
+  int e = gm::plan_create(&pl, A, 0, &p, s);
+  if (e) return e;
+  double* vtmp = nullptr;
+  const double* start = v0;
+  if (!start) {
+    if (cudaMalloc((void**)&vtmp, sizeof(double) * (size_t)A->n) != cudaSuccess) {
+      gm::plan_free(pl);
+      return GMRES_ERR_OOM;
+    }
+    gm::k_splitmix64<<<592, 256, 0, s>>>(vtmp, A->n, seed);
+    start = vtmp;
+  }
+  const int steps = degree + 1;
+  std::vector<double> H((size_t)(steps + 1) * steps);
+  int k = 0;
+  e = gm::plan_arnoldi(*pl, start, steps, nullptr, H.data(), &k, s);
+  cudaStreamSynchronize(s);
+  if (vtmp) cudaFree(vtmp);
+  gm::plan_free(pl);
+  if (e) return e;
+  if (k < 1) return GMRES_BREAKDOWN;
+  std::vector<double> Hk((size_t)(k + 1) * k);
+  for (int c = 0; c < k; ++c)
+    for (int i = 0; i <= k; ++i) Hk[i + (size_t)c * (k + 1)] = H[i + (size_t)c * (steps + 1)];
+  std::vector<double> wr, wi;
+  if (!gm::harmonic_ritz_values(Hk.data(), k, wr, wi)) return GMRES_BREAKDOWN;
+  gm::leja_order(wr, wi);
+  for (size_t i = 0; i < wr.size(); ++i) {
+    roots_re[i] = wr[i];
+    roots_im[i] = wi[i];
+  }
+  *nroots = (int32_t)wr.size();
+  return GMRES_OK;
+}
+
+int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream) {
+  if (!out || n < 0) return GMRES_ERR_INVALID;
+  if (n == 0) return GMRES_OK;
+  gm::k_splitmix64<<<592, 256, 0, (cudaStream_t)stream>>>(out, n, seed);
+  if (cudaGetLastError() != cudaSuccess) return GMRES_ERR_CUDA;
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Solver parity on the GPU: FP64 GMRES(m) and GMRES-IR through the C ABI against the CPU
+oracle on the same seeded systems, plus the status/edge cases of the boundary."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2109_01232_b300 as lib
+    lib.lib()
+    return lib
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def small():
+    return gen.config_small_2d()  # 64 x 64, Pe 10, manufactured solution
+
+
+def _dev(torch, *arrs):
+    return [torch.tensor(a, dtype=torch.float64, device="cuda") for a in arrs]
+
+
+def _relres(p, b, x):
+    return np.linalg.norm(b - oracle.spmv(p, x)) / np.linalg.norm(b)
+
+
+def test_fp64_gmres_small(g, torch, small):
+    p, b, x_true = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = g.gmres_solve(A, bt, xt, restart_m=50, rtol=1e-10)
+    x = xt.cpu().numpy()
+    xo, io = oracle.gmres(p, b, m=50, rtol=1e-10)
+    assert res.status == g.OK
+    assert res.relres <= 1e-10 and _relres(p, b, x) <= 1.0001e-10
+    assert abs(res.relres - _relres(p, b, x)) <= 1e-14
+    assert abs(res.iters - io.iters) <= 50
+    assert res.outer == io.outer or abs(res.outer - io.outer) <= 1
+
+
+def test_ir_fp32_small_matches_oracle(g, torch, small):
+    p, b, x_true = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = g.gmres_ir_solve(A, bt, xt, restart_m=50, rtol=1e-10, inner_prec="fp32")
+    x = xt.cpu().numpy()
+    xo, io = oracle.gmres_ir(p, b, m=50, rtol=1e-10, inner="fp32")
+    assert res.status == g.OK and res.relres <= 1e-10
+    assert _relres(p, b, x) <= 1.0001e-10
+    assert res.iters % 50 == 0  # outer test only at a restart (Section 3.2)
+    assert abs(res.iters - io.iters) <= 50
+    x64, i64 = oracle.gmres(p, b, m=50, rtol=1e-10)
+    assert i64.iters <= res.iters <= i64.iters + 100  # IR tracks FP64 GMRES (Section 5.2)
+
+
+@pytest.mark.parametrize("kind,prec,rtol", [("gmres", "fp64", 1e-13), ("ir", "fp32", 1e-12)])
+def test_solution_parity_to_1e8(g, torch, small, kind, prec, rtol):
+    """x agrees with the oracle's FP64 solution to 1e-8 when both are solved to a residual
+    that makes kappa * rtol < 1e-8 (kappa ~ 2e3 here)."""
+    p, b, x_true = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    fn = g.gmres_solve if kind == "gmres" else g.gmres_ir_solve
+    res = fn(A, bt, xt, restart_m=50, rtol=rtol, inner_prec=prec if prec != "fp64" else "fp32")
+    assert res.status == g.OK
+    xo, io = oracle.gmres(p, b, m=50, rtol=1e-13)
+    x = xt.cpu().numpy()
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-8
+    assert np.linalg.norm(x - x_true) / np.linalg.norm(x_true) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_ir_half_storage(g, torch, prec):
+    p, b, x_true = gen.config_small_2d(48)
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = g.gmres_ir_solve(A, bt, xt, restart_m=30, rtol=1e-10, inner_prec=prec)
+    assert res.status == g.OK and res.relres <= 1e-10
+    assert res.iters % 30 == 0
+    assert _relres(p, b, xt.cpu().numpy()) <= 1.0001e-10
+    _, io = oracle.gmres_ir(p, b, m=30, rtol=1e-10, inner=prec)
+    assert abs(res.iters - io.iters) <= 2 * 30 + io.iters // 4
+
+
+def test_ir_inner_tolerance(g, torch, small):
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = g.gmres_ir_solve(A, bt, xt, restart_m=50, rtol=1e-10, inner_rtol=1e-2)
+    assert res.status == g.OK and res.relres <= 1e-10
+    assert res.iters < res.outer * 50
+
+
+def test_plan_reuse_is_deterministic_and_matches_one_shot(g, torch, small):
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    plan = g.Plan(A, "ir", restart_m=40, rtol=1e-10)
+    outs = []
+    for _ in range(2):
+        bt, xt = _dev(torch, b, np.zeros(p.n))
+        r = plan.solve(bt, xt)
+        assert r.status == g.OK
+        outs.append((r.iters, xt.cpu().numpy()))
+    assert outs[0][0] == outs[1][0]
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])  # bitwise reproducible
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    r = g.gmres_ir_solve(A, bt, xt, restart_m=40, rtol=1e-10)
+    np.testing.assert_array_equal(xt.cpu().numpy(), outs[0][1])
+    # a second right-hand side on the same plan
+    b2 = oracle.spmv(p, np.ones(p.n))
+    bt, xt = _dev(torch, b2, np.zeros(p.n))
+    r2 = plan.solve(bt, xt)
+    assert r2.status == g.OK and _relres(p, b2, xt.cpu().numpy()) <= 1.0001e-10
+    plan.close()
+
+
+def test_host_pointer_api(g, torch, small):
+    p, b, _ = small
+    x = np.zeros(p.n)
+    r = g.gmres_ir_solve_host(p.row_ptr, p.col_idx, p.vals, b, x, restart_m=50)
+    assert r.status == g.OK and _relres(p, b, x) <= 1.0001e-10
+    x2 = np.zeros(p.n)
+    r2 = g.gmres_solve_host(p.row_ptr, p.col_idx, p.vals, b, x2, restart_m=50)
+    assert r2.status == g.OK and _relres(p, b, x2) <= 1.0001e-10
+
+
+def test_history_records_every_step(g, torch, small):
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    r = g.gmres_solve(A, bt, xt, restart_m=50, record_history=1, max_iters=5000)
+    assert len(r.history) == r.iters
+    _, io = oracle.gmres(p, b, m=50)
+    h = r.history[:50]
+    assert np.all(np.diff(h) <= 1e-15)  # GMRES residual is monotone within a cycle
+    np.testing.assert_allclose(h[:20], np.array(io.inner_hist[:20]), rtol=1e-8)
+
+
+# ------------------------------------------------------------ edge cases ----
+
+def test_zero_rhs_gives_zero(g, torch, small):
+    p, _, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, np.zeros(p.n), np.ones(p.n))
+    r = g.gmres_ir_solve(A, bt, xt)
+    assert r.status == g.OK and not xt.any().item()
+
+
+def test_nonfinite_input(g, torch, small):
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    bb = b.copy()
+    bb[17] = np.nan
+    for fn in (g.gmres_solve, g.gmres_ir_solve):
+        bt, xt = _dev(torch, bb, np.zeros(p.n))
+        assert fn(A, bt, xt).status == g.NONFINITE
+    vals = p.vals.copy()
+    vals[5] = np.inf
+    A2 = g.DeviceCSR(p.row_ptr, p.col_idx, vals, p.n)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    assert g.gmres_ir_solve(A2, bt, xt).status == g.NONFINITE
+
+
+def test_iteration_cap(g, torch, small):
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    r = g.gmres_solve(A, bt, xt, restart_m=5, max_iters=7, rtol=1e-14)
+    _, io = oracle.gmres(p, b, m=5, max_iters=7, rtol=1e-14)
+    assert r.status == g.NOT_CONVERGED == io.status and r.iters == 7 == io.iters
+    assert r.relres == pytest.approx(io.relres, rel=1e-9)
+
+
+def test_singular_breakdown_and_tiny_systems(g, torch):
+    S = gen.Problem("diag10", 2, np.array([0, 1, 1], np.int32), np.array([0], np.int32),
+                    np.array([1.0]))
+    A = g.DeviceCSR.from_problem(S)
+    bt, xt = _dev(torch, np.array([1.0, 1.0]), np.zeros(2))
+    assert g.gmres_solve(A, bt, xt, restart_m=2).status == g.BREAKDOWN
+    assert oracle.gmres(S, np.array([1.0, 1.0]), m=2)[1].status == oracle.BREAKDOWN
+    one = gen.Problem("one", 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    A1 = g.DeviceCSR.from_problem(one)
+    bt, xt = _dev(torch, np.array([6.0]), np.zeros(1))
+    r = g.gmres_ir_solve(A1, bt, xt)  # each cycle ends by a lucky breakdown after one step
+    assert r.status == g.OK and r.iters <= 3 and xt.item() == pytest.approx(2.0, rel=1e-12)
+    r = g.gmres_solve(A1, bt, xt.zero_())
+    assert r.status == g.OK and r.iters == 1 and xt.item() == pytest.approx(2.0, rel=1e-15)
+
+
+def test_identity_and_k_distinct_eigenvalues(g, torch):
+    d = np.repeat([1.0, 2.0, 5.0, 7.0, 11.0], 700)
+    n = d.size
+    D = gen.Problem("diag", n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    A = g.DeviceCSR.from_problem(D)
+    b = np.random.default_rng(3).uniform(1, 2, n)
+    bt, xt = _dev(torch, b, np.zeros(n))
+    r = g.gmres_solve(A, bt, xt, restart_m=30, rtol=1e-12)
+    assert r.status == g.OK and r.iters == 5
+    np.testing.assert_allclose(xt.cpu().numpy(), b / d, rtol=1e-11)
+    I = gen.Problem("eye", n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    bt, xt = _dev(torch, b, np.zeros(n))
+    r = g.gmres_solve(g.DeviceCSR.from_problem(I), bt, xt)
+    assert r.iters == 1 and np.allclose(xt.cpu().numpy(), b, rtol=1e-15)
+
+
+def test_invalid_csr_rejected(g, torch, small):
+    p, b, _ = small
+    cols = p.col_idx.copy()
+    cols[3] = p.n + 5
+    A = g.DeviceCSR(p.row_ptr, cols, p.vals, p.n)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    with pytest.raises(g.GmresError) as e:
+        g.gmres_ir_solve(A, bt, xt)
+    assert e.value.code == g.ERR_INVALID
+
+
+# ------------------------------------------------------- full-size case ----
+
+@pytest.fixture(scope="module")
+def cube():
+    return gen.config_3d(10.0)  # 100^3, 1M unknowns, 6.94M nonzeros
+
+
+def test_full_size_3d_ir_and_fp64(g, torch, cube):
+    """The benchmark's workload and launch configuration: both solvers reach 1e-10; the
+    explicit residual is recomputed by the oracle's SpMV; IR iterations are multiples of m."""
+    p, b = cube
+    A = g.DeviceCSR.from_problem(p)
+    out = {}
+    for kind in ("ir", "gmres"):
+        plan = g.Plan(A, kind, restart_m=50, rtol=1e-10, inner_prec="fp32", max_iters=20000)
+        bt, xt = _dev(torch, b, np.zeros(p.n))
+        r = plan.solve(bt, xt)
+        x = xt.cpu().numpy()
+        assert r.status == g.OK, (kind, r)
+        assert _relres(p, b, x) <= 1.0001e-10
+        out[kind] = (r, x)
+        plan.close()
+    assert out["ir"][0].iters % 50 == 0
+    assert out["ir"][0].iters <= out["gmres"][0].iters + 150
+    xi, xg = out["ir"][1], out["gmres"][1]
+    assert np.linalg.norm(xi - xg) / np.linalg.norm(xg) <= 1e-6
