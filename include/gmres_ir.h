@@ -158,6 +158,23 @@ int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V
 int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const double* v0,
                      double* roots_re, double* roots_im, int32_t* nroots, void* stream);
 
+/* Profiling aid for the per-kernel time breakdown of one cycle (the kernel
+ * classes of the paper's Section 5.2 breakdown and Table 1: SpMV, the two
+ * transposed/plain GEMV passes of CGS2, norm, least squares, update).  Runs
+ * the FP64 residual of x0 (DEVICE, n doubles) against b (DEVICE) and one
+ * restart cycle kernel by kernel, not through the graph, with CUDA events
+ * around every launch.  ms_out: HOST, 3m+3 doubles; ms_out[3j+0/1/2] = fused
+ * SpMV / first CGS update / second CGS update of Arnoldi step j,
+ * ms_out[3m+0/1/2] = least squares / x update / residual; -1 for steps the
+ * cycle did not reach. */
+int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0, double* ms_out,
+                             void* stream);
+
+/* Plan geometry: info_out (HOST, 8 int64) = n, nnz, leading dimension ld,
+ * m, storage precision, grid of the SpMV kernel, grid of the CGS kernels,
+ * grid of the residual kernel. */
+int gmres_plan_info(gmres_plan plan, int64_t* info_out);
+
 /* SplitMix64 vector on the device: out[i] in [-1, 1) (DEVICE, n doubles). */
 int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
 

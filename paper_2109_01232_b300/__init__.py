@@ -74,6 +74,8 @@ _SIGNATURES = {
     "gmres_poly_roots": (ctypes.c_int, [ctypes.POINTER(csr_t), _I32, _U64, _P, _P, _P,
                                         ctypes.POINTER(_I32), _P]),
     "gmres_splitmix64_fill": (ctypes.c_int, [_P, _I64, _U64, _P]),
+    "gmres_plan_profile_cycle": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gmres_plan_info": (ctypes.c_int, [_P, _P]),
 }
 
 
@@ -206,10 +208,14 @@ def _solve_host(fn_name, row_ptr, col_idx, vals, b, x, stream=None, **kw) -> Sol
     """Host-memory variant: numpy (or pinned torch CPU) arrays; x is updated in place."""
     p = default_params(**kw)
     st, hist = _stats(p)
-    arrs = [np.ascontiguousarray(row_ptr, np.int32), np.ascontiguousarray(col_idx, np.int32),
-            np.ascontiguousarray(vals, np.float64)]
-    c = csr_t(len(arrs[0]) - 1, len(arrs[2]), arrs[0].ctypes.data, arrs[1].ctypes.data,
-              arrs[2].ctypes.data)
+    def host(a, dtype):  # torch CPU tensors (e.g. pinned) are passed without a copy
+        if hasattr(a, "data_ptr"):
+            return a, int(a.data_ptr()), int(a.numel())
+        a = np.ascontiguousarray(a, dtype)
+        return a, a.ctypes.data, a.size
+
+    keep = [host(row_ptr, np.int32), host(col_idx, np.int32), host(vals, np.float64)]
+    c = csr_t(keep[0][2] - 1, keep[2][2], keep[0][1], keep[1][1], keep[2][1])
     bp = b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data
     xp = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
     code = getattr(lib(), fn_name)(ctypes.byref(c), bp, xp, ctypes.byref(p), ctypes.byref(st),
@@ -272,6 +278,22 @@ class Plan:
         _check(lib().gmres_plan_arnoldi(self.handle, _ptr(v0), steps, _ptr(V), H.ctypes.data,
                                         ctypes.byref(k), _stream(stream)), "arnoldi")
         return V, H.T.copy(), int(k.value)
+
+    def info(self) -> dict:
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib().gmres_plan_info(self.handle, out.ctypes.data), "plan_info")
+        keys = ["n", "nnz", "ld", "m", "prec", "grid_spmv", "grid_vec", "grid_res"]
+        return dict(zip(keys, map(int, out)))
+
+    def profile_cycle(self, b, x0, stream=None) -> np.ndarray:
+        """Per-launch device times (ms) of one cycle run kernel by kernel, shape (m+1, 3):
+        row j = (SpMV, first CGS update, second CGS update) of step j, last row = (least
+        squares, x update, residual); -1 where the cycle ended earlier."""
+        m = int(self.params.restart_m)
+        out = np.zeros(3 * m + 3, dtype=np.float64)
+        _check(lib().gmres_plan_profile_cycle(self.handle, _ptr(b), _ptr(x0), out.ctypes.data,
+                                              _stream(stream)), "profile_cycle")
+        return out.reshape(m + 1, 3)
 
     def close(self):
         if self.handle:

@@ -65,8 +65,10 @@ struct Plan {
 // ---------------------------------------------------------------------------
 // Kernel launch sequences (templated on the storage precision).
 // ---------------------------------------------------------------------------
+// Kernel `which` (0: fused SpMV + first-pass dots, 1: first CGS update + second-pass dots,
+// 2: second CGS update + norm + Givens) of Arnoldi step j.
 template <int P>
-static void launch_step(Plan& pl, int j, cudaStream_t s) {
+static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   S* V = (S*)pl.V;
@@ -74,20 +76,29 @@ static void launch_step(Plan& pl, int j, cudaStream_t s) {
   W* w2 = (W*)pl.w2;
   W* w3 = (W*)pl.w3;
   W* part = (W*)pl.part;
-  const double rs = pl.a_scale / pl.v_scale;
-  const size_t sm1 = SpmvSmem<P>::bytes(j + 2);
-  if (j == 0)
-    k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, sm1, s>>>(
-        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, pl.r, pl.v_scale, V, 0,
-        w1, part, pl.st, pl.arr.h1);
-  else
-    k_spmv_arnoldi<P, W><<<pl.grid_spmv, NT, sm1, s>>>(
-        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, w3, pl.v_scale, V, j, w1,
-        part, pl.st, pl.arr.h1);
-  k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
-      V, pl.ld, j, pl.v_scale, w1, w2, part, pl.st, pl.arr.h1, pl.arr.h2);
-  k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1), s>>>(V, pl.ld, j, pl.v_scale, w2, w3,
-                                                                   part, pl.st, pl.arr);
+  if (which == 0) {
+    const double rs = pl.a_scale / pl.v_scale;
+    const size_t sm1 = SpmvSmem<P>::bytes(j + 2);
+    if (j == 0)
+      k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, pl.r, pl.v_scale, V, 0,
+          w1, part, pl.st, pl.arr.h1);
+    else
+      k_spmv_arnoldi<P, W><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, w3, pl.v_scale, V, j, w1,
+          part, pl.st, pl.arr.h1);
+  } else if (which == 1) {
+    k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
+        V, pl.ld, j, pl.v_scale, w1, w2, part, pl.st, pl.arr.h1, pl.arr.h2);
+  } else {
+    k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1), s>>>(V, pl.ld, j, pl.v_scale, w2,
+                                                                     w3, part, pl.st, pl.arr);
+  }
+}
+
+template <int P>
+static void launch_step(Plan& pl, int j, cudaStream_t s) {
+  for (int which = 0; which < 3; ++which) launch_step_kernel<P>(pl, j, which, s);
 }
 
 static void launch_residual(Plan& pl, int first, cudaStream_t s) {
@@ -96,14 +107,23 @@ static void launch_residual(Plan& pl, int first, cudaStream_t s) {
                                                        pl.arr, first);
 }
 
+// Kernel `which` of the cycle's end (0: least squares, 1: x update, 2: FP64 residual).
 template <int P>
-static void launch_cycle_tail(Plan& pl, cudaStream_t s) {
+static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  k_lsq<<<1, 32, 0, s>>>(pl.st, pl.arr);
-  k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
-                                                             pl.st, pl.arr.y, pl.xb);
-  launch_residual(pl, 0, s);
+  if (which == 0)
+    k_lsq<<<1, 32, 0, s>>>(pl.st, pl.arr);
+  else if (which == 1)
+    k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
+                                                               pl.st, pl.arr.y, pl.xb);
+  else
+    launch_residual(pl, 0, s);
+}
+
+template <int P>
+static void launch_cycle_tail(Plan& pl, cudaStream_t s) {
+  for (int which = 0; which < 3; ++which) launch_tail_kernel<P>(pl, which, s);
 }
 
 template <int P>
@@ -455,6 +475,55 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
   return pl.h_st->status == ST_NONFINITE ? GMRES_NONFINITE : GMRES_OK;
 }
 
+// One restart cycle launched kernel by kernel (not through the graph), each launch
+// bracketed by CUDA events on `s`.  ms_out[3j + {0,1,2}] = the three kernels of step j,
+// ms_out[3m + {0,1,2}] = least squares / x update / residual; -1 for the steps that the
+// cycle did not reach.  The host reads the cycle flag after every step.
+int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_out, cudaStream_t s) {
+  const int m = pl.m, nslots = 3 * m + 3;
+  const size_t nb = sizeof(double) * (size_t)pl.n;
+  init_state(pl, *pl.h_st);
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(pl.bb, b, nb, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(pl.xb, x0, nb, cudaMemcpyDeviceToDevice, s));
+  launch_residual(pl, 1, s);
+  std::vector<cudaEvent_t> ev(2 * (size_t)nslots, nullptr);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  std::vector<int> ran(nslots, 0);
+  int* h_flag = &pl.h_st->cycle_done;
+  int err = dispatch(pl.prec, [&](auto PP) -> int {
+    constexpr int P = decltype(PP)::value;
+    for (int j = 0; j < m; ++j) {
+      for (int w = 0; w < 3; ++w) {
+        const int sl = 3 * j + w;
+        cudaEventRecord(ev[2 * sl], s);
+        launch_step_kernel<P>(pl, j, w, s);
+        cudaEventRecord(ev[2 * sl + 1], s);
+        ran[sl] = 1;
+      }
+      cudaMemcpyAsync(h_flag, &pl.st->cycle_done, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) return GMRES_ERR_CUDA;
+      if (*h_flag) break;
+    }
+    for (int w = 0; w < 3; ++w) {
+      const int sl = 3 * m + w;
+      cudaEventRecord(ev[2 * sl], s);
+      launch_tail_kernel<P>(pl, w, s);
+      cudaEventRecord(ev[2 * sl + 1], s);
+      ran[sl] = 1;
+    }
+    return cudaGetLastError() == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
+  });
+  if (err == GMRES_OK && cudaStreamSynchronize(s) != cudaSuccess) err = GMRES_ERR_CUDA;
+  for (int i = 0; i < nslots; ++i) {
+    float ms = -1.f;
+    if (err == GMRES_OK && ran[i]) cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+    ms_out[i] = ran[i] ? (double)ms : -1.0;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return err;
+}
+
 }  // namespace gm
 
 using gm::Plan;
@@ -530,6 +599,20 @@ int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V
                        int32_t* k_out, void* stream) {
   if (!plan) return GMRES_ERR_INVALID;
   return gm::plan_arnoldi(*plan->pl, v0, steps, V_out, H_out, k_out, (cudaStream_t)stream);
+}
+
+int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0, double* ms_out,
+                             void* stream) {
+  if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
+  return gm::plan_profile_cycle(*plan->pl, b, x0, ms_out, (cudaStream_t)stream);
+}
+
+int gmres_plan_info(gmres_plan plan, int64_t* info_out) {
+  if (!plan || !info_out) return GMRES_ERR_INVALID;
+  const Plan& pl = *plan->pl;
+  const int64_t v[8] = {pl.n, pl.A.nnz, pl.ld, pl.m, pl.prec, pl.grid_spmv, pl.grid_vec, pl.grid_res};
+  for (int i = 0; i < 8; ++i) info_out[i] = v[i];
+  return GMRES_OK;
 }
 
 static int solve_once(const gmres_csr* A, const double* b, double* x, const gmres_params* p, int kind,
