@@ -158,6 +158,18 @@ int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V
 int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const double* v0,
                      double* roots_re, double* roots_im, int32_t* nroots, void* stream);
 
+/* y = p(A) v with the plan's GMRES polynomial (Section 3.4; the plan must have
+ * poly_degree > 0): the product form over the Leja-ordered roots, d SpMVs with
+ * the plan's inner copy of A, in the working precision.  v: DEVICE, n doubles;
+ * y: DEVICE, n values of the working type (double for FP64 plans, float
+ * otherwise). */
+int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream);
+
+/* The plan's polynomial roots (HOST arrays of at least poly_degree+1 entries,
+ * either may be NULL) in the order they are applied; *nroots = 0 without a
+ * preconditioner. */
+int gmres_plan_poly_roots(gmres_plan plan, double* roots_re, double* roots_im, int32_t* nroots);
+
 /* Profiling aid for the per-kernel time breakdown of one cycle (the kernel
  * classes of the paper's Section 5.2 breakdown and Table 1: SpMV, the two
  * transposed/plain GEMV passes of CGS2, norm, least squares, update).  Runs

@@ -76,6 +76,8 @@ _SIGNATURES = {
     "gmres_splitmix64_fill": (ctypes.c_int, [_P, _I64, _U64, _P]),
     "gmres_plan_profile_cycle": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gmres_plan_info": (ctypes.c_int, [_P, _P]),
+    "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
 }
 
 
@@ -278,6 +280,22 @@ class Plan:
         _check(lib().gmres_plan_arnoldi(self.handle, _ptr(v0), steps, _ptr(V), H.ctypes.data,
                                         ctypes.byref(k), _stream(stream)), "arnoldi")
         return V, H.T.copy(), int(k.value)
+
+    def poly_apply(self, v, stream=None):
+        """y = p(A) v with the plan's GMRES polynomial (working dtype)."""
+        torch = _torch()
+        y = torch.empty(self.A.n, dtype=self.work_dtype, device="cuda")
+        _check(lib().gmres_plan_poly_apply(self.handle, _ptr(v), _ptr(y), _stream(stream)),
+               "poly_apply")
+        return y
+
+    def roots(self) -> np.ndarray:
+        n = ctypes.c_int32(0)
+        _check(lib().gmres_plan_poly_roots(self.handle, None, None, ctypes.byref(n)), "roots")
+        re, im = np.zeros(n.value), np.zeros(n.value)
+        _check(lib().gmres_plan_poly_roots(self.handle, re.ctypes.data, im.ctypes.data,
+                                           ctypes.byref(n)), "roots")
+        return re + 1j * im
 
     def info(self) -> dict:
         out = np.zeros(8, dtype=np.int64)

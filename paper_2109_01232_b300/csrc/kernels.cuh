@@ -105,8 +105,11 @@ struct SpmvSmem {
 //   w = (a_scale / v_scale) * A_stored * V[:, j]      (= A v_j)
 //   h1[c] = v_c . w  (c <= j),  wnorm = ||w||
 // src is the FP64 residual (j = 0) or the previous step's w'' (working type).
+// PLAIN: src is already the vector to multiply (p(A) v_j with a polynomial
+// preconditioner, working type, unscaled): it is gathered as is and V[:, j], stored
+// by the polynomial's first kernel, is not written.
 // ---------------------------------------------------------------------------
-template <int P, class SrcT>
+template <int P, class SrcT, bool PLAIN = false>
 __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     const int* __restrict__ rp, const int* __restrict__ ci, const typename Tr<P>::S* __restrict__ av,
     int n, long long ld, double row_scale_d, const SrcT* __restrict__ src, double v_scale,
@@ -133,7 +136,10 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
   const SrcT f = (SrcT)(v_scale * st->sigma);
   const W row_scale = (W)row_scale_d;
   auto make = [&](SrcT x) -> S { return to_s<S>(f * x); };
-  auto xval = [&](int c) -> W { return to_w(make(src[c])); };
+  auto xval = [&](int c) -> W {
+    if constexpr (PLAIN) return (W)src[c];
+    else return to_w(make(src[c]));
+  };
   S* Vj = V + (long long)j * ld;
 
   const int ntiles = (n + TR - 1) / TR;
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
       const int row = r0 + tid + k * NT;
-      if (row < n) Vj[row] = make(src[row]);
+      if (!PLAIN && row < n) Vj[row] = make(src[row]);
     }
     W a[VEC];
     tile_spmv<S, W, TR, CAP>(rp, ci, av, n, r0, rp_s, prod_s, xval, a);

@@ -16,6 +16,7 @@
 
 #include "gmres_ir.h"
 #include "kernels.cuh"
+#include "poly_kernels.cuh"
 #include "poly_host.h"
 
 namespace gm {
@@ -31,6 +32,12 @@ static int map_err(cudaError_t e) {
   } while (0)
 
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+struct PolyOp {
+  int pair;       // 0: real root, 1: conjugate pair
+  int last;       // last operation: the prod update is skipped
+  double c1, c2;
+};
 
 struct Plan {
   int kind = 1;  // 0: FP64 GMRES, 1: GMRES-IR
@@ -59,14 +66,79 @@ struct Plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // polynomial preconditioner (right, p(A) in product form)
   std::vector<double> roots_re, roots_im;
+  std::vector<PolyOp> poly;         // product-form program built from the roots
+  void *pa = nullptr, *pb = nullptr, *pt = nullptr, *py = nullptr;  // working-type vectors
+  int grid_elem = 1;
   double t_setup_ms = 0.0;
 };
+
+// Product-form program of p(A) from Leja-ordered roots: a real root contributes one
+// operation (c1 = 1/theta), a conjugate pair a +- ib one operation (c1 = 2a/q, c2 = 1/q,
+// q = a^2 + b^2).
+static std::vector<PolyOp> poly_program(const std::vector<double>& re, const std::vector<double>& im) {
+  std::vector<PolyOp> ops;
+  for (size_t i = 0; i < re.size();) {
+    PolyOp op{};
+    if (im[i] == 0.0) {
+      op.pair = 0;
+      op.c1 = 1.0 / re[i];
+      i += 1;
+    } else {
+      const double q = re[i] * re[i] + im[i] * im[i];
+      op.pair = 1;
+      op.c1 = 2.0 * re[i] / q;
+      op.c2 = 1.0 / q;
+      i += 2;
+    }
+    ops.push_back(op);
+  }
+  if (!ops.empty()) ops.back().last = 1;
+  return ops;
+}
 
 // ---------------------------------------------------------------------------
 // Kernel launch sequences (templated on the storage precision).
 // ---------------------------------------------------------------------------
-// Kernel `which` (0: fused SpMV + first-pass dots, 1: first CGS update + second-pass dots,
-// 2: second CGS update + norm + Givens) of Arnoldi step j.
+
+// y = p(A) prod0 (prod0 is pl.pa, overwritten; pl.pb / pl.pt are scratch).
+template <int P>
+static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  const size_t sm = sizeof(W) * SpmvSmem<P>::CAP + sizeof(int) * (SpmvSmem<P>::TR + 1) + 16;
+  W* cur = (W*)pl.pa;
+  W* nxt = (W*)pl.pb;
+  W* y = (W*)pl.py;
+  W* t = (W*)pl.pt;
+  int first = 1;
+  for (const PolyOp& op : pl.poly) {
+    if (!op.pair) {
+      if (op.last) {
+        k_poly_axpy<P><<<pl.grid_elem, NT, 0, s>>>(cur, y, pl.n, op.c1, first, pl.st, in_cycle);
+      } else {
+        k_poly_spmv<P, POLY_REAL><<<pl.grid_spmv, NT, sm, s>>>(
+            pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, nullptr, y, nxt,
+            op.c1, 0.0, first, pl.st, in_cycle);
+        std::swap(cur, nxt);
+      }
+    } else {
+      k_poly_spmv<P, POLY_PAIR_A><<<pl.grid_spmv, NT, sm, s>>>(
+          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, nullptr, y,
+          op.last ? nullptr : t, op.c1, op.c2, first, pl.st, in_cycle);
+      if (!op.last) {
+        k_poly_spmv<P, POLY_PAIR_B><<<pl.grid_spmv, NT, sm, s>>>(
+            pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, t, nullptr, nxt,
+            op.c1, op.c2, 0, pl.st, in_cycle);
+        std::swap(cur, nxt);
+      }
+    }
+    first = 0;
+  }
+}
+
+// Kernel `which` (0: fused SpMV + first-pass dots -- with a polynomial preconditioner the
+// whole w = A p(A) v_j chain --, 1: first CGS update + second-pass dots, 2: second CGS
+// update + norm + Givens) of Arnoldi step j.
 template <int P>
 static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
@@ -77,8 +149,21 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   W* w3 = (W*)pl.w3;
   W* part = (W*)pl.part;
   if (which == 0) {
-    const double rs = pl.a_scale / pl.v_scale;
     const size_t sm1 = SpmvSmem<P>::bytes(j + 2);
+    if (!pl.poly.empty()) {
+      if (j == 0)
+        k_poly_start<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
+                                                           (W*)pl.pa, pl.st);
+      else
+        k_poly_start<P, W><<<pl.grid_elem, NT, 0, s>>>(w3, pl.v_scale, pl.n, V, pl.ld, j,
+                                                      (W*)pl.pa, pl.st);
+      launch_poly<P>(pl, 1, s);
+      k_spmv_arnoldi<P, W, true><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, pl.a_scale, (const W*)pl.py,
+          pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1);
+      return;
+    }
+    const double rs = pl.a_scale / pl.v_scale;
     if (j == 0)
       k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, pl.r, pl.v_scale, V, 0,
@@ -107,18 +192,27 @@ static void launch_residual(Plan& pl, int first, cudaStream_t s) {
                                                        pl.arr, first);
 }
 
-// Kernel `which` of the cycle's end (0: least squares, 1: x update, 2: FP64 residual).
+// Kernel `which` of the cycle's end (0: least squares, 1: x update -- x += gamma p(A) V y
+// with a preconditioner --, 2: FP64 residual).
 template <int P>
 static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  if (which == 0)
+  if (which == 0) {
     k_lsq<<<1, 32, 0, s>>>(pl.st, pl.arr);
-  else if (which == 1)
-    k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
-                                                               pl.st, pl.arr.y, pl.xb);
-  else
+  } else if (which == 1) {
+    if (!pl.poly.empty()) {
+      k_vy<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
+                                                               pl.st, pl.arr.y, (W*)pl.pa);
+      launch_poly<P>(pl, 0, s);
+      k_xadd<P><<<pl.grid_elem, NT, 0, s>>>((const W*)pl.py, pl.xb, pl.n, pl.st);
+    } else {
+      k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld,
+                                                                 pl.v_scale, pl.st, pl.arr.y, pl.xb);
+    }
+  } else {
     launch_residual(pl, 0, s);
+  }
 }
 
 template <int P>
@@ -141,8 +235,18 @@ static int configure(Plan& pl) {
                           (int)sm_max));
   CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_max));
+  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_max));
+  const size_t sm_poly = sizeof(W) * SpmvSmem<P>::CAP + sizeof(int) * (SpmvSmem<P>::TR + 1) + 16;
+  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_poly));
+  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_PAIR_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_poly));
+  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_poly));
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
   CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_u1));
+  pl.grid_elem = pl.sms * 8;
   int occ = 1;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_arnoldi<P, W>, NT, sm_max));
   const long long ntiles = (pl.n + SpmvSmem<P>::TR - 1) / SpmvSmem<P>::TR;
@@ -191,6 +295,10 @@ static void plan_free(Plan* pl) {
   cudaFree(pl->xb);
   cudaFree(pl->bb);
   cudaFree(pl->part);
+  cudaFree(pl->pa);
+  cudaFree(pl->pb);
+  cudaFree(pl->pt);
+  cudaFree(pl->py);
   cudaFree(pl->st);
   cudaFree(pl->arr_mem);
   if (pl->h_st) cudaFreeHost(pl->h_st);
@@ -330,7 +438,6 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   cudaEventDestroy(t1);
 
   // Polynomial preconditioner roots (set-up, FP64 Arnoldi on the GPU + host eigenvalues).
-  if (p->poly_degree > 0) return fail(GMRES_ERR_INVALID);  // applied in the cycle: not built yet
   if (p->poly_degree > 0) {
     std::vector<double> re(p->poly_degree + 1), im(p->poly_degree + 1);
     int nr = 0;
@@ -339,6 +446,12 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     if (e) return fail(e);
     pl->roots_re.assign(re.begin(), re.begin() + nr);
     pl->roots_im.assign(im.begin(), im.begin() + nr);
+    pl->poly = poly_program(pl->roots_re, pl->roots_im);
+    if ((e = alloc(&pl->pa, wb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->pb, wb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->pt, wb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->py, wb * (size_t)ld))) return fail(e);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GMRES_ERR_CUDA);
     pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
   }
 
@@ -419,6 +532,22 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
 // ---------------------------------------------------------------------------
 // Test entry points on a plan.
 // ---------------------------------------------------------------------------
+int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
+  if (pl.poly.empty() || !v || !y) return GMRES_ERR_INVALID;
+  init_state(pl, *pl.h_st);
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  int e = dispatch(pl.prec, [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    using W = typename Tr<P>::W;
+    k_load_work<P><<<pl.grid_elem, NT, 0, s>>>(v, (W*)pl.pa, pl.n);
+    launch_poly<P>(pl, 0, s);
+    return (int)cudaMemcpyAsync(y, pl.py, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
+  });
+  if (e) return GMRES_ERR_CUDA;
+  CK(cudaStreamSynchronize(s));
+  return GMRES_OK;
+}
+
 int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
@@ -605,6 +734,22 @@ int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0,
                              void* stream) {
   if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
   return gm::plan_profile_cycle(*plan->pl, b, x0, ms_out, (cudaStream_t)stream);
+}
+
+int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  return gm::plan_poly_apply(*plan->pl, v, y, (cudaStream_t)stream);
+}
+
+int gmres_plan_poly_roots(gmres_plan plan, double* roots_re, double* roots_im, int32_t* nroots) {
+  if (!plan || !nroots) return GMRES_ERR_INVALID;
+  const Plan& pl = *plan->pl;
+  *nroots = (int32_t)pl.roots_re.size();
+  for (size_t i = 0; i < pl.roots_re.size(); ++i) {
+    if (roots_re) roots_re[i] = pl.roots_re[i];
+    if (roots_im) roots_im[i] = pl.roots_im[i];
+  }
+  return GMRES_OK;
 }
 
 int gmres_plan_info(gmres_plan plan, int64_t* info_out) {
