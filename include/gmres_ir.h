@@ -100,6 +100,9 @@ typedef struct {
 
 void gmres_default_params(gmres_params* p);
 const char* gmres_status_string(int status);
+/* The last CUDA failure recorded by this thread (call site and the runtime's
+ * message) behind a GMRES_ERR_CUDA / GMRES_ERR_OOM status; "" if none. */
+const char* gmres_last_error(void);
 
 /* FP64 restarted GMRES(m) (Algorithm 1 with CGS2).  b: DEVICE, n doubles.
  * x: DEVICE, n doubles, initial guess on entry, solution on exit.  The cycle
@@ -189,6 +192,7 @@ int gmres_plan_info(gmres_plan plan, int64_t* info_out);
 
 /* SplitMix64 vector on the device: out[i] in [-1, 1) (DEVICE, n doubles). */
 int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
+
 
 #ifdef __cplusplus
 }

@@ -26,8 +26,8 @@ MAX_POLY_DEGREE = 96
 
 
 class GmresError(RuntimeError):
-    def __init__(self, code: int, what: str):
-        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+    def __init__(self, code: int, what: str, detail: str = ""):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})" + (f" [{detail}]" if detail else ""))
         self.code = code
 
 
@@ -57,6 +57,7 @@ _I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c
 _SIGNATURES = {
     "gmres_default_params": (None, [ctypes.POINTER(params_t)]),
     "gmres_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmres_last_error": (ctypes.c_char_p, []),
     "gmres_solve": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t),
                                    ctypes.POINTER(stats_t), _P]),
     "gmres_ir_solve": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t),
@@ -120,7 +121,10 @@ def _ptr(t) -> int:
 
 def _check(code: int, what: str, allowed=(OK,)):
     if code not in allowed:
-        raise GmresError(code, what)
+        detail = ""
+        if code in (ERR_CUDA, ERR_OOM) and _lib is not None:
+            detail = (_lib.gmres_last_error() or b"").decode(errors="replace")
+        raise GmresError(code, what, detail)
     return code
 
 
@@ -343,3 +347,4 @@ def splitmix64(n: int, seed: int, stream=None):
     out = torch.empty(n, dtype=torch.float64, device="cuda")
     _check(lib().gmres_splitmix64_fill(_ptr(out), n, seed, _stream(stream)), "splitmix64")
     return out
+

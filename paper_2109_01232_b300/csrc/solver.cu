@@ -10,7 +10,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -21,15 +23,26 @@
 
 namespace gm {
 
-static int map_err(cudaError_t e) {
+// The last CUDA failure seen by this thread (call site and runtime message), reported by
+// gmres_last_error().
+static thread_local char g_last_error[256] = "";
+
+static int note_cuda(cudaError_t e, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "solver.cu:%d: %s: %s", line, cudaGetErrorName(e),
+           cudaGetErrorString(e));
   cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA;
 }
-#define CK(x)                                     \
-  do {                                            \
-    cudaError_t e_ = (x);                         \
-    if (e_ != cudaSuccess) return map_err(e_);    \
+#define CK(x)                                                 \
+  do {                                                        \
+    cudaError_t e_ = (x);                                     \
+    if (e_ != cudaSuccess) return note_cuda(e_, __LINE__);    \
   } while (0)
+// Evaluates a CUDA call; on failure records it and yields the status code, else 0.
+#define CUDA_STATUS(x) ([&]() -> int {                        \
+    cudaError_t e_ = (x);                                     \
+    return e_ == cudaSuccess ? 0 : note_cuda(e_, __LINE__);   \
+  }())
 
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
 
@@ -230,13 +243,16 @@ template <int P>
 static int configure(Plan& pl) {
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
+  // The attributes are per kernel, shared by every plan: set them for the largest restart
+  // length so that a plan with a smaller m never lowers them under another plan.
+  const size_t sm_attr = SpmvSmem<P>::bytes(LSQ_MAX + 2);
   const size_t sm_max = SpmvSmem<P>::bytes(pl.m + 2);
   CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_max));
+                          (int)sm_attr));
   CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_max));
+                          (int)sm_attr));
   CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_max));
+                          (int)sm_attr));
   const size_t sm_poly = sizeof(W) * SpmvSmem<P>::CAP + sizeof(int) * (SpmvSmem<P>::TR + 1) + 16;
   CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_poly));
@@ -245,7 +261,8 @@ static int configure(Plan& pl) {
   CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_poly));
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
-  CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_u1));
+  CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(W) * (size_t)(LSQ_MAX + 1) * (1 + NWARP))));
   pl.grid_elem = pl.sms * 8;
   int occ = 1;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_arnoldi<P, W>, NT, sm_max));
@@ -356,7 +373,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   pl->p = *p;
   pl->ld = round_up(std::max(A->n, 1), TILE_MAX);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  if (int e_ = CUDA_STATUS(cudaGetDevice(&dev))) return fail(e_);
   cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
   if (int e = check_csr_device(A, s)) return fail(e);
 
@@ -367,8 +384,8 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   const size_t sb = storage_bytes(pl->prec), wb = work_bytes(pl->prec);
   const long long ld = pl->ld, m = pl->m;
   auto alloc = [&](void** ptr, size_t bytes) -> int {
-    if (cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) return map_err(cudaErrorMemoryAllocation);
-    if (cudaMemsetAsync(*ptr, 0, std::max<size_t>(bytes, 16), s) != cudaSuccess) return GMRES_ERR_CUDA;
+    if (int e_ = CUDA_STATUS(cudaMalloc(ptr, std::max<size_t>(bytes, 16)))) return e_;
+    if (int e_ = CUDA_STATUS(cudaMemsetAsync(*ptr, 0, std::max<size_t>(bytes, 16), s))) return e_;
     return GMRES_OK;
   };
   int e = GMRES_OK;
@@ -406,7 +423,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
       k_absmax<<<pl->sms * 4, 256, 0, s>>>(A->vals, A->nnz, d_mx);
       unsigned long long bits = 0;
       cudaMemcpyAsync(&bits, d_mx, 8, cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) { cudaFree(d_mx); return fail(GMRES_ERR_CUDA); }
+      if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) { cudaFree(d_mx); return fail(e_); }
       cudaFree(d_mx);
       double mx;
       memcpy(&mx, &bits, 8);
@@ -430,7 +447,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   const int gmax = std::max({pl->grid_spmv, pl->grid_vec, pl->grid_res});
   if ((e = alloc(&pl->part, 8 * (size_t)(m + 2) * gmax))) return fail(e);
   cudaEventRecord(t1, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, t0, t1);
   pl->t_setup_ms = ms;
@@ -451,22 +468,22 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     if ((e = alloc(&pl->pb, wb * (size_t)ld))) return fail(e);
     if ((e = alloc(&pl->pt, wb * (size_t)ld))) return fail(e);
     if ((e = alloc(&pl->py, wb * (size_t)ld))) return fail(e);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+    if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
     pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
   }
 
   // Capture one restart cycle as a CUDA graph.
-  if (cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(GMRES_ERR_CUDA);
-  if (cudaEventCreate(&pl->ev0) != cudaSuccess || cudaEventCreate(&pl->ev1) != cudaSuccess)
-    return fail(GMRES_ERR_CUDA);
-  if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return fail(GMRES_ERR_CUDA);
+  if (int e_ = CUDA_STATUS(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking))) return fail(e_);
+  if (int e_ = CUDA_STATUS(cudaEventCreate(&pl->ev0))) return fail(e_);
+  if (int e_ = CUDA_STATUS(cudaEventCreate(&pl->ev1))) return fail(e_);
+  if (int e_ = CUDA_STATUS(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal)))
+    return fail(e_);
   dispatch(pl->prec, [&](auto P) {
     launch_cycle<decltype(P)::value>(*pl, pl->cap);
     return 0;
   });
-  if (cudaStreamEndCapture(pl->cap, &pl->graph) != cudaSuccess) return fail(GMRES_ERR_CUDA);
-  if (cudaGraphInstantiate(&pl->exec, pl->graph, 0) != cudaSuccess) return fail(GMRES_ERR_CUDA);
+  if (int e_ = CUDA_STATUS(cudaStreamEndCapture(pl->cap, &pl->graph))) return fail(e_);
+  if (int e_ = CUDA_STATUS(cudaGraphInstantiate(&pl->exec, pl->graph, 0))) return fail(e_);
   *out = pl;
   return GMRES_OK;
 }
@@ -543,7 +560,7 @@ int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
     launch_poly<P>(pl, 0, s);
     return (int)cudaMemcpyAsync(y, pl.py, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
   });
-  if (e) return GMRES_ERR_CUDA;
+  if (e) return note_cuda((cudaError_t)e, __LINE__);
   CK(cudaStreamSynchronize(s));
   return GMRES_OK;
 }
@@ -560,7 +577,7 @@ int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
         pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, (W*)pl.part, pl.st, pl.arr.h1);
     return (int)cudaMemcpyAsync(y, pl.w1, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
   });
-  if (e) return GMRES_ERR_CUDA;
+  if (e) return note_cuda((cudaError_t)e, __LINE__);
   CK(cudaStreamSynchronize(s));
   return GMRES_OK;
 }
@@ -587,7 +604,7 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
                                                    steps, pl.st);
     return (int)cudaGetLastError();
   });
-  if (e) return GMRES_ERR_CUDA;
+  if (e) return note_cuda((cudaError_t)e, __LINE__);
   CK(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int k = pl.h_st->k;
@@ -631,7 +648,7 @@ int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_o
         ran[sl] = 1;
       }
       cudaMemcpyAsync(h_flag, &pl.st->cycle_done, sizeof(int), cudaMemcpyDeviceToHost, s);
-      if (cudaStreamSynchronize(s) != cudaSuccess) return GMRES_ERR_CUDA;
+      if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return e_;
       if (*h_flag) break;
     }
     for (int w = 0; w < 3; ++w) {
@@ -675,6 +692,8 @@ void gmres_default_params(gmres_params* p) {
   p->seed = 0;
   p->record_history = 0;
 }
+
+const char* gmres_last_error(void) { return gm::g_last_error; }
 
 const char* gmres_status_string(int status) {
   switch (status) {
@@ -896,3 +915,4 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream) {
 }
 
 }  // extern "C"
+
