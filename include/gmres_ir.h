@@ -193,6 +193,25 @@ int gmres_plan_info(gmres_plan plan, int64_t* info_out);
 /* SplitMix64 vector on the device: out[i] in [-1, 1) (DEVICE, n doubles). */
 int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
 
+/* y = A v in FP64 without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- code whose GPU memory is owned by another allocator that reserved it up
+ * front, latency-critical loops that cannot take the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree, and plug-ins that may not allocate.
+ * It runs the same fused SpMV kernel as gmres_plan_spmv on an FP64 plan, so y
+ * equals that call's result; its scratch (the kernel's state, partial sums and
+ * one vector of n doubles) lives in a fixed device array of about 8.1 MB that
+ * every GPU loading this library keeps until the process exits.
+ *   A: DEVICE CSR (FP64 values), n <= GMRES_NOALLOC_MAX_N, else
+ *      GMRES_ERR_TOO_LARGE (checked before any device work).
+ *   v: DEVICE, n doubles; y: DEVICE, n doubles (must not overlap v).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the one array: calls that may overlap on
+ * the GPU (different streams, or several host threads) race and must be
+ * serialised by the caller.  Returns after the stream has finished the work. */
+#define GMRES_NOALLOC_MAX_N (1 << 20)
+int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, double* y, void* stream);
 
 #ifdef __cplusplus
 }

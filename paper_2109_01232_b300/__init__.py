@@ -79,7 +79,9 @@ _SIGNATURES = {
     "gmres_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
+    "gmres_spmv_fp64_noalloc": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, _P]),
 }
+NOALLOC_MAX_N = 1 << 20
 
 
 def lib() -> ctypes.CDLL:
@@ -348,3 +350,11 @@ def splitmix64(n: int, seed: int, stream=None):
     _check(lib().gmres_splitmix64_fill(_ptr(out), n, seed, _stream(stream)), "splitmix64")
     return out
 
+
+def spmv_fp64_noalloc(A: DeviceCSR, v, y, stream=None) -> None:
+    """y = A v in FP64 through gmres_spmv_fp64_noalloc, which allocates no device memory
+    (for callers whose GPU memory belongs to another allocator or that must not trigger
+    cudaMalloc's implicit synchronisation).  v, y: float64 CUDA tensors of length n."""
+    c = A.c()
+    _check(lib().gmres_spmv_fp64_noalloc(ctypes.byref(c), _ptr(v), _ptr(y), _stream(stream)),
+           "spmv_fp64_noalloc")

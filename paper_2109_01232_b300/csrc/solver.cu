@@ -916,3 +916,97 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream) {
 
 }  // extern "C"
 
+// ===========================================================================
+// FP64 SpMV that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code whose device memory is owned by another
+// allocator that reserved the GPU up front, latency-critical loops that cannot afford
+// the implicit device synchronisation of cudaMalloc/cudaFree, and plug-ins that are not
+// allowed to allocate at all.  gmres_spmv_fp64_noalloc runs the same fused SpMV kernel
+// as gmres_plan_spmv on an FP64 plan, with its scratch (the kernel's device state,
+// per-CTA partial sums and the basis column it writes) in the file-scope array below.
+// Every GPU that loads this library holds that array until the process exits.
+// ===========================================================================
+namespace gm {
+namespace {
+
+constexpr int kNoAllocGrid = 1184;  // CTAs per launch at most (8 per SM on 148 SMs)
+constexpr long long kNoAllocRows =
+    ((long long)GMRES_NOALLOC_MAX_N + TILE_MAX - 1) / TILE_MAX * TILE_MAX;
+
+struct NoAllocHead {
+  DevState st;                      // flags, scale and tickets read by the kernel
+  double h1[4];                     // the kernel's dot products (not returned)
+  double part[2 * kNoAllocGrid];    // per-CTA partial sums
+};
+constexpr size_t kNoAllocHeadBytes = (sizeof(NoAllocHead) + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocHeadBytes + sizeof(double) * (size_t)kNoAllocRows;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Clears what the kernel needs to start from zero (flags, reduction ticket) and sets the
+// source scale to 1, so the input vector is multiplied as given.
+__global__ void k_noalloc_reset(DevState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *st = DevState{};
+    st->sigma = 1.0;
+  }
+}
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_scratch(void** out, int* sms) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GMRES_ERR_CUDA;
+    }
+    int count = 0;
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return GMRES_ERR_CUDA;
+    }
+    g_noalloc_sms[dev] = count > 0 ? count : 1;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return GMRES_OK;
+}
+
+}  // namespace
+}  // namespace gm
+
+extern "C" int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, double* y,
+                                       void* stream) {
+  if (!A || A->n < 0 || A->nnz < 0 || !v || !y) return GMRES_ERR_INVALID;
+  if (A->n > GMRES_NOALLOC_MAX_N) return GMRES_ERR_TOO_LARGE;
+  if (A->n == 0) return GMRES_OK;
+  if (!A->row_ptr || !A->vals || (A->nnz > 0 && !A->col_idx)) return GMRES_ERR_INVALID;
+  void* base = nullptr;
+  int sms = 1;
+  if (int e = gm::noalloc_scratch(&base, &sms)) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto* head = reinterpret_cast<gm::NoAllocHead*>(base);
+  double* vcol = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + gm::kNoAllocHeadBytes);
+  constexpr int TR = gm::SpmvSmem<0>::TR;
+  const int ntiles = (A->n + TR - 1) / TR;
+  const int grid = std::max(1, std::min({ntiles, sms * 8, gm::kNoAllocGrid}));
+  gm::k_noalloc_reset<<<1, 1, 0, s>>>(&head->st);
+  gm::k_spmv_arnoldi<0, double><<<grid, gm::NT, gm::SpmvSmem<0>::bytes(2), s>>>(
+      A->row_ptr, A->col_idx, A->vals, A->n, gm::kNoAllocRows, 1.0, v, 1.0, vcol, 0, y,
+      head->part, &head->st, head->h1);
+  if (cudaGetLastError() != cudaSuccess) return GMRES_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
+}
