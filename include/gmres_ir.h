@@ -198,8 +198,9 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
  * -- code whose GPU memory is owned by another allocator that reserved it up
  * front, latency-critical loops that cannot take the implicit device-wide
  * synchronisation of cudaMalloc/cudaFree, and plug-ins that may not allocate.
- * It runs the same fused SpMV kernel as gmres_plan_spmv on an FP64 plan, so y
- * equals that call's result; its scratch (the kernel's state, partial sums and
+ * It runs the CSR form of the fused SpMV kernel behind gmres_plan_spmv (plans
+ * use a SELL-32 copy of A, which this entry point cannot allocate), so y agrees
+ * with gmres_plan_spmv on an FP64 plan to rounding; its scratch (the kernel's state, partial sums and
  * one vector of n doubles) lives in a fixed device array of about 8.1 MB that
  * every GPU loading this library keeps until the process exits.
  *   A: DEVICE CSR (FP64 values), n <= GMRES_NOALLOC_MAX_N, else

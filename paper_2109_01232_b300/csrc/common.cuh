@@ -10,10 +10,11 @@
 
 namespace gm {
 
-constexpr int NT = 256;           // threads per CTA of the streaming kernels
+constexpr int NT = 512;           // threads per CTA of the streaming kernels
 constexpr int NWARP = NT / 32;
 constexpr int LSQ_MAX = 512;      // largest restart length (GMRES_MAX_RESTART)
-constexpr int TILE_MAX = 2048;    // largest SpMV row tile; every buffer's leading dimension
+constexpr int LSQ_PACKED_MAX = 200;  // R staged in shared memory up to this m (160 KB)
+constexpr int TILE_MAX = 4096;    // largest SpMV row tile; every buffer's leading dimension
                                   // is a multiple of it, so tiles never cross the padding
 
 // Precision of the inner cycle: S = storage type of the Krylov basis and of the

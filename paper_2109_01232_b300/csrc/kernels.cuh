@@ -89,11 +89,156 @@ __device__ __forceinline__ bool arrive_last(unsigned int* ticket, int* s_last) {
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// SELL-32 engine (the inner copy of A built at plan set-up): rows are grouped in
+// slices of 32 consecutive rows; slice s stores its entries column-major, entry e of
+// row 32s + l at meta[s].x + 32 e + l, padded to the slice's longest row
+// (meta[s].y) with zero values and an in-range column.  A warp owns whole slices, so
+// every load of values and column indices is one coalesced 128-byte access and a row
+// needs no shared memory or barrier.  Computes the rows r0 + tid + k*NT (k < RPT).
+// ---------------------------------------------------------------------------
+template <class AT, class W, int RPT, class XF>
+__device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const int* __restrict__ sc,
+                                          const AT* __restrict__ sv, int nslices, int r0,
+                                          const XF& xval, W (&acc)[RPT]) {
+  const int lane = threadIdx.x & 31;
+  const int s0 = (r0 >> 5) + (threadIdx.x >> 5);
+  int2 mt[RPT];
+  int maxw = 0;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int s = s0 + k * NWARP;
+    mt[k] = s < nslices ? meta[s] : make_int2(0, 0);
+    maxw = max(maxw, mt[k].y);
+    acc[k] = W(0);
+  }
+#pragma unroll 4
+  for (int e = 0; e < maxw; ++e) {
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      if (e < mt[k].y) {
+        const int idx = mt[k].x + e * 32 + lane;
+        acc[k] += to_w(sv[idx]) * xval(sc[idx]);
+      }
+    }
+  }
+}
+
+// Sum of the G per-CTA partials p[0..G) by one warp, four independent load streams per
+// lane (fixed order, so the result is reproducible).
+template <class W>
+__device__ __forceinline__ W warp_sum_partials(const W* __restrict__ p, int G) {
+  const int lane = threadIdx.x & 31;
+  W s0 = W(0), s1 = W(0), s2 = W(0), s3 = W(0);
+  int b = lane;
+  for (; b + 96 < G; b += 128) {
+    s0 += __ldcg(&p[b]);
+    s1 += __ldcg(&p[b + 32]);
+    s2 += __ldcg(&p[b + 64]);
+    s3 += __ldcg(&p[b + 96]);
+  }
+  for (; b < G; b += 32) s0 += __ldcg(&p[b]);
+  return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// Reduces ncol columns of per-CTA partials part[c * G + b] with the whole CTA and calls
+// out(c, sum) once per column (lane 0 of the warp that owns it).  Warp w owns columns
+// w, w + NWARP, ...; each lane keeps four columns' loads in flight.  Fixed order.
+template <class W, class F>
+__device__ __forceinline__ void block_reduce_columns(const W* __restrict__ part, int ncol, int G,
+                                                     const F& out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = warp; c0 < ncol; c0 += 4 * NWARP) {
+    W s[4] = {W(0), W(0), W(0), W(0)};
+#pragma unroll 4
+    for (int b = lane; b < G; b += 32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + q * NWARP;
+        if (c < ncol) s[q] += __ldcg(&part[(long long)c * G + b]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + q * NWARP;
+      const W v = warp_sum(s[q]);
+      if (c < ncol && lane == 0) out(c, v);
+    }
+  }
+}
+
+// w[q] -= sum_{b < B} coef[c0 + b] * V[c0 + b][base + q]: the B column vectors are loaded
+// before any is used, so B 16-byte loads per thread are in flight.
+template <int B, class S, class W, int VEC>
+__device__ __forceinline__ void update_cols(const S* __restrict__ V, long long ld, long long base,
+                                            int c0, const W* __restrict__ coef, W (&wv)[VEC]) {
+  S v[B][VEC];
+#pragma unroll
+  for (int b = 0; b < B; ++b) ldv(V + (long long)(c0 + b) * ld + base, v[b]);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const W k = coef[c0 + b];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) wv[q] -= k * to_w(v[b][q]);
+  }
+}
+
+// d[b] = sum_q V[c0 + b][base + q] * w[q] for b < B (B loads in flight).
+template <int B, class S, class W, int VEC>
+__device__ __forceinline__ void dot_cols(const S* __restrict__ V, long long ld, long long base, int c0,
+                                         const W (&wv)[VEC], W (&d)[B]) {
+  S v[B][VEC];
+#pragma unroll
+  for (int b = 0; b < B; ++b) ldv(V + (long long)(c0 + b) * ld + base, v[b]);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    W t = W(0);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) t += to_w(v[b][q]) * wv[q];
+    d[b] = t;
+  }
+}
+
+// Dot products of w with the nc columns V[0..nc) for this thread's rows, summed over the
+// warp and added to acc[warp * stride + c] by lane 0.
+template <class S, class W, int VEC>
+__device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long ld, long long base,
+                                            int nc, const W (&wv)[VEC], W* acc) {
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  for (; c + 8 <= nc; c += 8) {
+    W d[8];
+    dot_cols<8>(V, ld, base, c, wv, d);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) d[b] = warp_sum(d[b]);
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[c + b] += d[b];
+    }
+  }
+  for (; c < nc; ++c) {
+    W d[1];
+    dot_cols<1>(V, ld, base, c, wv, d);
+    const W t = warp_sum(d[0]);
+    if (lane == 0) acc[c] += t;
+  }
+}
+
+// w -= V[0..nc) coef for this thread's rows.
+template <class S, class W, int VEC>
+__device__ __forceinline__ void update_all(const S* __restrict__ V, long long ld, long long base,
+                                           int nc, const W* __restrict__ coef, W (&wv)[VEC]) {
+  int c = 0;
+  for (; c + 8 <= nc; c += 8) update_cols<8>(V, ld, base, c, coef, wv);
+  for (; c < nc; ++c) update_cols<1>(V, ld, base, c, coef, wv);
+}
+
 template <int P>
 struct SpmvSmem {
   using W = typename Tr<P>::W;
   static constexpr int TR = NT * Tr<P>::VEC;
-  static constexpr int CAP = TR * 8;
+  static constexpr int CAP = 4096;  // CSR engine: nonzeros staged per chunk
+  // dynamic shared memory of k_spmv_arnoldi (CSR: staged products and row pointers)
   static size_t bytes(int ncol) {
     return sizeof(W) * (size_t)(CAP + TR + NWARP * ncol) + sizeof(int) * (size_t)(TR + 1) + 16;
   }
@@ -108,6 +253,7 @@ struct SpmvSmem {
 // PLAIN: src is already the vector to multiply (p(A) v_j with a polynomial
 // preconditioner, working type, unscaled): it is gathered as is and V[:, j], stored
 // by the polynomial's first kernel, is not written.
+// The matrix is CSR (rp, ci, av); plans use the SELL-32 form k_spmv_sell below.
 // ---------------------------------------------------------------------------
 template <int P, class SrcT, bool PLAIN = false>
 __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
@@ -169,36 +315,7 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     W nrm = W(0);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
-    int c = 0;
-    for (; c + 4 <= j + 1; c += 4) {
-      S v0[VEC], v1[VEC], v2[VEC], v3[VEC];
-      ldv(V + (long long)c * ld + gb, v0);
-      ldv(V + (long long)(c + 1) * ld + gb, v1);
-      ldv(V + (long long)(c + 2) * ld + gb, v2);
-      ldv(V + (long long)(c + 3) * ld + gb, v3);
-      W d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        d0 += to_w(v0[q]) * wv[q];
-        d1 += to_w(v1[q]) * wv[q];
-        d2 += to_w(v2[q]) * wv[q];
-        d3 += to_w(v3[q]) * wv[q];
-      }
-      d0 = warp_sum(d0); d1 = warp_sum(d1); d2 = warp_sum(d2); d3 = warp_sum(d3);
-      if (lane == 0) {
-        W* ac = acc + warp * ncol + c;
-        ac[0] += d0; ac[1] += d1; ac[2] += d2; ac[3] += d3;
-      }
-    }
-    for (; c <= j; ++c) {
-      S v0[VEC];
-      ldv(V + (long long)c * ld + gb, v0);
-      W d0 = 0;
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) d0 += to_w(v0[q]) * wv[q];
-      d0 = warp_sum(d0);
-      if (lane == 0) acc[warp * ncol + c] += d0;
-    }
+    dots_to_acc<S, W, VEC>(V, ld, gb, j + 1, wv, acc + warp * ncol);
     nrm = warp_sum(nrm);
     if (lane == 0) acc[warp * ncol + j + 1] += nrm;
     __syncthreads();
@@ -210,15 +327,126 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     part[(long long)c * G + blockIdx.x] = s;
   }
   if (!arrive_last(&st->ticket[0], &s_last)) return;
-  for (int c = warp; c < ncol; c += NWARP) {
-    W s = W(0);
-    for (int b = lane; b < G; b += 32) s += __ldcg(&part[(long long)c * G + b]);
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (c <= j) h1[c] = (double)s / v_scale;
-      else st->wnorm = sqrt((double)s);
+  block_reduce_columns(part, ncol, G, [&](int c, W s) {
+    if (c <= j) h1[c] = (double)s / v_scale;
+    else st->wnorm = sqrt((double)s);
+  });
+  if (tid == 0) st->ticket[0] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Step kernel 1 on the SELL-32 copy, warp-independent form.  A warp owns "warp tiles" of
+// WT = 32 VEC consecutive rows (VEC slices): it stores its rows of V[:, j], computes its
+// rows of w = A v_j slice by slice, turns them from the slice layout (lane l holds rows
+// 32q + l) into the vector layout (lane l holds rows VEC l .. VEC l + VEC-1) through a
+// warp-private buffer, and accumulates the first-pass dot products over its rows.  There
+// is no CTA barrier inside the loop, so warps at different phases overlap.  Each warp
+// handles `tpw` consecutive warp tiles; the grid is sized so all warps get the same count.
+// Shared memory per warp: WT + (j+2) working values.
+// ---------------------------------------------------------------------------
+template <int P>
+struct SellSmem {
+  using W = typename Tr<P>::W;
+  static constexpr int WT = 32 * Tr<P>::VEC;
+  static size_t bytes(int ncol) { return sizeof(W) * (size_t)NWARP * (WT + ncol) + 16; }
+};
+
+template <int P, class SrcT, bool PLAIN>
+__global__ void __launch_bounds__(NT) k_spmv_sell(
+    const int2* __restrict__ meta, const int* __restrict__ sc, const typename Tr<P>::S* __restrict__ sv,
+    int nslices, int n, long long ld, double row_scale_d, const SrcT* __restrict__ src,
+    double v_scale, typename Tr<P>::S* V, int j, typename Tr<P>::W* __restrict__ wout,
+    typename Tr<P>::W* __restrict__ part, DevState* st, double* __restrict__ h1, int tpw) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  constexpr int VEC = Tr<P>::VEC;
+  constexpr int WT = SellSmem<P>::WT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ncol = j + 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  W* ws = reinterpret_cast<W*>(smem_raw) + (size_t)warp * (WT + ncol);
+  W* acc = ws + WT;
+  __shared__ int s_skip, s_last;
+  if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
+  __syncthreads();
+  if (s_skip) return;
+  for (int c = lane; c < ncol; c += 32) acc[c] = W(0);
+  __syncwarp();
+
+  const SrcT f = (SrcT)(v_scale * st->sigma);
+  const W row_scale = (W)row_scale_d;
+  auto make = [&](SrcT x) -> S { return to_s<S>(f * x); };
+  auto xval = [&](int c) -> W {
+    if constexpr (PLAIN) return (W)src[c];
+    else return to_w(make(src[c]));
+  };
+  S* Vj = V + (long long)j * ld;
+  const int nwt = (n + WT - 1) / WT;
+  const int gw = blockIdx.x * NWARP + warp;
+  for (int t = 0; t < tpw; ++t) {
+    const int wt = gw * tpw + t;
+    if (wt >= nwt) break;
+    const int r0 = wt * WT;
+    const int s0 = r0 >> 5;
+    int2 mt[VEC];
+    int maxw = 0;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      mt[q] = s0 + q < nslices ? meta[s0 + q] : make_int2(0, 0);
+      maxw = max(maxw, mt[q].y);
     }
+    if constexpr (!PLAIN) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        const int row = r0 + 32 * q + lane;
+        if (row < n) Vj[row] = make(src[row]);
+      }
+    }
+    W a[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a[q] = W(0);
+#pragma unroll 4
+    for (int e = 0; e < maxw; ++e) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        if (e < mt[q].y) {
+          const int idx = mt[q].x + e * 32 + lane;
+          a[q] += to_w(sv[idx]) * xval(sc[idx]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      const int row = r0 + 32 * q + lane;
+      const W wv = row < n ? row_scale * a[q] : W(0);
+      ws[32 * q + lane] = wv;
+      if (row < n) wout[row] = wv;
+    }
+    __syncwarp();
+    W wv[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) wv[q] = ws[VEC * lane + q];
+    __syncwarp();
+    W nrm = W(0);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
+    dots_to_acc<S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc);
+    nrm = warp_sum(nrm);
+    if (lane == 0) acc[j + 1] += nrm;
   }
+  __syncthreads();
+  const int G = gridDim.x;
+  W* acc0 = reinterpret_cast<W*>(smem_raw) + WT;
+  for (int c = tid; c < ncol; c += NT) {
+    W s = W(0);
+    for (int w = 0; w < NWARP; ++w) s += acc0[(size_t)w * (WT + ncol) + c];
+    part[(long long)c * G + blockIdx.x] = s;
+  }
+  if (!arrive_last(&st->ticket[0], &s_last)) return;
+  block_reduce_columns(part, ncol, G, [&](int c, W s) {
+    if (c <= j) h1[c] = (double)s / v_scale;
+    else st->wnorm = sqrt((double)s);
+  });
   if (tid == 0) st->ticket[0] = 0;
 }
 
@@ -254,7 +482,7 @@ __global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restri
   W* coef = reinterpret_cast<W*>(smem_raw);
   W* acc = coef + nc;
   __shared__ int s_skip, s_last;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
   if (s_skip) return;
@@ -266,62 +494,9 @@ __global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restri
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
-    int c = 0;
-    for (; c + 4 <= nc; c += 4) {
-      S v0[VEC], v1[VEC], v2[VEC], v3[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      ldv(V + (long long)(c + 1) * ld + base, v1);
-      ldv(V + (long long)(c + 2) * ld + base, v2);
-      ldv(V + (long long)(c + 3) * ld + base, v3);
-      const W k0 = coef[c], k1 = coef[c + 1], k2 = coef[c + 2], k3 = coef[c + 3];
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        W t = wv[q];
-        t -= k0 * to_w(v0[q]);
-        t -= k1 * to_w(v1[q]);
-        t -= k2 * to_w(v2[q]);
-        t -= k3 * to_w(v3[q]);
-        wv[q] = t;
-      }
-    }
-    for (; c < nc; ++c) {
-      S v0[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      const W k0 = coef[c];
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) wv[q] -= k0 * to_w(v0[q]);
-    }
+    update_all<S, W, VEC>(V, ld, base, nc, coef, wv);
     stv(wout + base, wv);
-    c = 0;
-    for (; c + 4 <= nc; c += 4) {
-      S v0[VEC], v1[VEC], v2[VEC], v3[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      ldv(V + (long long)(c + 1) * ld + base, v1);
-      ldv(V + (long long)(c + 2) * ld + base, v2);
-      ldv(V + (long long)(c + 3) * ld + base, v3);
-      W d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        d0 += to_w(v0[q]) * wv[q];
-        d1 += to_w(v1[q]) * wv[q];
-        d2 += to_w(v2[q]) * wv[q];
-        d3 += to_w(v3[q]) * wv[q];
-      }
-      d0 = warp_sum(d0); d1 = warp_sum(d1); d2 = warp_sum(d2); d3 = warp_sum(d3);
-      if (lane == 0) {
-        W* ac = acc + warp * nc + c;
-        ac[0] += d0; ac[1] += d1; ac[2] += d2; ac[3] += d3;
-      }
-    }
-    for (; c < nc; ++c) {
-      S v0[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      W d0 = 0;
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) d0 += to_w(v0[q]) * wv[q];
-      d0 = warp_sum(d0);
-      if (lane == 0) acc[warp * nc + c] += d0;
-    }
+    dots_to_acc<S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
   }
   __syncthreads();
   const int G = gridDim.x;
@@ -331,58 +506,74 @@ __global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restri
     part[(long long)c * G + blockIdx.x] = s;
   }
   if (!arrive_last(&st->ticket[1], &s_last)) return;
-  for (int c = warp; c < nc; c += NWARP) {
-    W s = W(0);
-    for (int b = lane; b < G; b += 32) s += __ldcg(&part[(long long)c * G + b]);
-    s = warp_sum(s);
-    if (lane == 0) h2[c] = (double)s / v_scale;
-  }
+  block_reduce_columns(part, nc, G, [&](int c, W s) { h2[c] = (double)s / v_scale; });
   if (tid == 0) st->ticket[1] = 0;
 }
 
 // Givens update of column j (Algorithm 1's least-squares problem solved
-// incrementally, FP64, one thread).  Sets the cycle/solve flags.
-__device__ void givens_step(DevState* st, const Arrays& a, int j, double hn) {
+// incrementally, FP64).  Called by one whole warp: the lanes stage the new column
+// (h1 + h2, ||w''||) and the previous rotations in shared memory `sh` (3 (j+2) doubles)
+// with parallel loads, lane 0 applies the rotations and sets the cycle/solve flags,
+// and the lanes write the unrotated and rotated columns back.
+__device__ void givens_step_warp(DevState* st, const Arrays& a, int j, double hn, double* sh) {
+  const int lane = threadIdx.x & 31;
   const int m = st->m;
   const int ldh = m + 1;
+  double* col = sh;              // j+2 entries
+  double* cs = sh + (j + 2);     // j entries
+  double* sn = cs + (j + 1);     // j entries
+  for (int i = lane; i <= j; i += 32) {
+    col[i] = a.h1[i] + a.h2[i];
+    if (i < j) {
+      cs[i] = a.cs[i];
+      sn[i] = a.sn[i];
+    }
+  }
+  if (lane == 0) col[j + 1] = hn;
+  __syncwarp();
   double* Hc = a.H + (long long)j * ldh;
+  for (int i = lane; i <= j + 1; i += 32) Hc[i] = col[i];
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double x = col[j], y = hn;
+    double c = 1.0, s = 0.0;
+    if (y != 0.0) {
+      const double rho = hypot(x, y);
+      c = x / rho;
+      s = y / rho;
+    }
+    col[j] = c * x + s * y;
+    col[j + 1] = 0.0;
+    a.cs[j] = c;
+    a.sn[j] = s;
+    const double gj = a.g[j];
+    a.g[j + 1] = -s * gj;
+    a.g[j] = c * gj;
+    const long long iters = st->iters + 1;
+    st->k = j + 1;
+    st->iters = iters;
+    const double res = fabs(s * gj);
+    if (iters <= st->hist_cap)
+      a.hist[iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
+    if (!isfinite(hn) || !isfinite(res) || !isfinite(col[j])) {
+      st->status = ST_NONFINITE;
+      st->stop = 1;
+      st->cycle_done = 1;
+    } else {
+      const int brk = hn <= 16.0 * st->u_work * st->wnorm;
+      st->breakdown = brk;
+      if (brk || res <= st->stop_rel || j + 1 >= m || iters >= st->max_iters) st->cycle_done = 1;
+      st->sigma = brk ? 0.0 : 1.0 / hn;
+    }
+  }
+  __syncwarp();
   double* Rc = a.R + (long long)j * ldh;
-  for (int i = 0; i <= j; ++i) Hc[i] = a.h1[i] + a.h2[i];
-  Hc[j + 1] = hn;
-  for (int i = 0; i <= j + 1; ++i) Rc[i] = Hc[i];
-  for (int i = 0; i < j; ++i) {
-    const double t = a.cs[i] * Rc[i] + a.sn[i] * Rc[i + 1];
-    Rc[i + 1] = -a.sn[i] * Rc[i] + a.cs[i] * Rc[i + 1];
-    Rc[i] = t;
-  }
-  const double x = Rc[j], y = hn;
-  double c = 1.0, s = 0.0;
-  if (y != 0.0) {
-    const double rho = hypot(x, y);
-    c = x / rho;
-    s = y / rho;
-  }
-  Rc[j] = c * x + s * y;
-  Rc[j + 1] = 0.0;
-  a.cs[j] = c;
-  a.sn[j] = s;
-  a.g[j + 1] = -s * a.g[j];
-  a.g[j] = c * a.g[j];
-  st->k = j + 1;
-  st->iters += 1;
-  const double res = fabs(a.g[j + 1]);
-  if (st->iters <= st->hist_cap)
-    a.hist[st->iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
-  if (!isfinite(hn) || !isfinite(res) || !isfinite(Rc[j])) {
-    st->status = ST_NONFINITE;
-    st->stop = 1;
-    st->cycle_done = 1;
-    return;
-  }
-  const int brk = hn <= 16.0 * st->u_work * st->wnorm;
-  st->breakdown = brk;
-  if (brk || res <= st->stop_rel || j + 1 >= m || st->iters >= st->max_iters) st->cycle_done = 1;
-  st->sigma = brk ? 0.0 : 1.0 / hn;
+  for (int i = lane; i <= j + 1; i += 32) Rc[i] = col[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -415,31 +606,7 @@ __global__ void __launch_bounds__(NT) k_cgs_u2(const typename Tr<P>::S* __restri
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
-    int c = 0;
-    for (; c + 4 <= nc; c += 4) {
-      S v0[VEC], v1[VEC], v2[VEC], v3[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      ldv(V + (long long)(c + 1) * ld + base, v1);
-      ldv(V + (long long)(c + 2) * ld + base, v2);
-      ldv(V + (long long)(c + 3) * ld + base, v3);
-      const W k0 = coef[c], k1 = coef[c + 1], k2 = coef[c + 2], k3 = coef[c + 3];
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        W t = wv[q];
-        t -= k0 * to_w(v0[q]);
-        t -= k1 * to_w(v1[q]);
-        t -= k2 * to_w(v2[q]);
-        t -= k3 * to_w(v3[q]);
-        wv[q] = t;
-      }
-    }
-    for (; c < nc; ++c) {
-      S v0[VEC];
-      ldv(V + (long long)c * ld + base, v0);
-      const W k0 = coef[c];
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) wv[q] -= k0 * to_w(v0[q]);
-    }
+    update_all<S, W, VEC>(V, ld, base, nc, coef, wv);
     stv(wout + base, wv);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
@@ -455,45 +622,69 @@ __global__ void __launch_bounds__(NT) k_cgs_u2(const typename Tr<P>::S* __restri
   }
   if (!arrive_last(&st->ticket[2], &s_last)) return;
   if (warp == 0) {
-    W s = W(0);
-    for (int b = lane; b < G; b += 32) s += __ldcg(&part[b]);
-    s = warp_sum(s);
-    if (lane == 0) {
-      st->ticket[2] = 0;
-      givens_step(st, arr, j, sqrt((double)s));
+    __shared__ double gsh[3 * (LSQ_MAX + 2)];
+    W s0 = W(0), s1 = W(0), s2 = W(0), s3 = W(0);
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      s0 += __ldcg(&part[b]);
+      s1 += __ldcg(&part[b + 32]);
+      s2 += __ldcg(&part[b + 64]);
+      s3 += __ldcg(&part[b + 96]);
     }
+    for (; b < G; b += 32) s0 += __ldcg(&part[b]);
+    const W s = warp_sum((s0 + s1) + (s2 + s3));
+    if (lane == 0) st->ticket[2] = 0;
+    givens_step_warp(st, arr, j, sqrt((double)s), gsh);
   }
 }
 
 // ---------------------------------------------------------------------------
-// End of a cycle: least squares R y = g by back substitution (one warp, FP64).
+// End of a cycle: least squares R y = g by back substitution (FP64, one warp solves).
 // A trailing diagonal entry below 16 u max|R| is dropped (singular factor).
-// ---------------------------------------------------------------------------
-__global__ void k_lsq(DevState* st, Arrays a) {
+// R is staged in shared memory (packed upper triangle, column by column) when
+// `packed` is set (m <= LSQ_PACKED_MAX); the loads are spread over all threads.
+__global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Rs = reinterpret_cast<double*>(smem_raw);
   __shared__ double gw[LSQ_MAX];
-  __shared__ int s_kk;
-  const int lane = threadIdx.x;
-  if (read_flag(&st->stop)) return;
+  __shared__ double red[NWARP];
+  __shared__ int s_kk, s_skip;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_skip = read_flag(&st->stop);
+  __syncthreads();
+  if (s_skip) return;
   const int k = st->k, ldh = st->m + 1;
+  auto rix = [](int i, int c) { return c * (c + 1) / 2 + i; };
   double rmax = 0.0;
-  for (int c = lane; c < k; c += 32)
-    for (int i = 0; i <= c; ++i) rmax = fmax(rmax, fabs(a.R[i + (long long)c * ldh]));
+  for (int c = warp; c < k; c += NWARP)
+    for (int i = lane; i <= c; i += 32) {
+      const double v = a.R[i + (long long)c * ldh];
+      if (packed) Rs[rix(i, c)] = v;
+      rmax = fmax(rmax, fabs(v));
+    }
   rmax = warp_max(rmax);
-  if (lane == 0) {
+  if (lane == 0) red[warp] = rmax;
+  for (int i = tid; i < k; i += NT) gw[i] = a.g[i];
+  __syncthreads();
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < NWARP; ++w) mx = fmax(mx, red[w]);
     int kk = k;
-    while (kk > 0 && fabs(a.R[(kk - 1) + (long long)(kk - 1) * ldh]) <= 16.0 * st->u_work * rmax) --kk;
+    auto diag = [&](int i) { return packed ? Rs[rix(i, i)] : a.R[i + (long long)i * ldh]; };
+    while (kk > 0 && fabs(diag(kk - 1)) <= 16.0 * st->u_work * mx) --kk;
     s_kk = kk;
     st->k_used = kk;
     st->singular = kk < k;
   }
-  __syncwarp();
+  __syncthreads();
+  if (warp != 0) return;
   const int kk = s_kk;
-  for (int i = lane; i < kk; i += 32) gw[i] = a.g[i];
-  __syncwarp();
   for (int i = kk - 1; i >= 0; --i) {
-    const double yi = gw[i] / a.R[i + (long long)i * ldh];
+    const double rii = packed ? Rs[rix(i, i)] : a.R[i + (long long)i * ldh];
+    const double yi = gw[i] / rii;
     __syncwarp();
-    for (int l = lane; l < i; l += 32) gw[l] -= a.R[l + (long long)i * ldh] * yi;
+    for (int l = lane; l < i; l += 32)
+      gw[l] -= (packed ? Rs[rix(l, i)] : a.R[l + (long long)i * ldh]) * yi;
     if (lane == 0) a.y[i] = yi;
     __syncwarp();
   }
@@ -553,7 +744,7 @@ __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict
 // "r_{i+1} = b - A x_{i+1} [double]").
 // ---------------------------------------------------------------------------
 constexpr int RES_TR = NT * 2;
-constexpr int RES_CAP = RES_TR * 8;
+constexpr int RES_CAP = 4096;  // nonzeros staged per chunk (32 KB)
 inline size_t residual_smem() { return sizeof(double) * RES_CAP + sizeof(int) * (RES_TR + 1) + 16; }
 
 __global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, const int* __restrict__ ci,
@@ -658,6 +849,34 @@ __global__ void k_cast_vals(const double* __restrict__ v, S* __restrict__ out, l
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nnz;
        i += (long long)gridDim.x * blockDim.x)
     out[i] = to_s<S>(v[i] / scale);
+}
+
+// Fill the SELL-32 copy from CSR: one thread per (padded) row.  Values are divided by
+// `scale` and rounded to the storage type; padding entries get value 0 and an in-range
+// column (the row itself, or 0 past the last row).
+template <class S>
+__global__ void k_build_sell(const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ v, int n, const int2* __restrict__ meta,
+                             int nslices, double scale, int* __restrict__ sc, S* __restrict__ sv) {
+  const long long total = (long long)nslices * 32;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(r >> 5), l = (int)(r & 31);
+    const int2 mt = meta[s];
+    const int base = r < n ? rp[r] : 0;
+    const int len = r < n ? rp[r + 1] - base : 0;
+    const int pad_col = r < n ? (int)r : 0;
+    for (int e = 0; e < mt.y; ++e) {
+      const long long idx = (long long)mt.x + (long long)e * 32 + l;
+      if (e < len) {
+        sc[idx] = ci[base + e];
+        sv[idx] = to_s<S>(v[base + e] / scale);
+      } else {
+        sc[idx] = pad_col;
+        sv[idx] = to_s<S>(0.0);
+      }
+    }
+  }
 }
 
 // CSR structure check: row_ptr[0] = 0, row_ptr[n] = nnz, nondecreasing, 0 <= col < n.

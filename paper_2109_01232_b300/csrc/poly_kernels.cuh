@@ -6,10 +6,10 @@
 //   pair a +- ib, q = a^2+b^2: t = A prod;  y += (2a/q) prod - t/q;
 //                            prod <- prod - (2a/q) t + (A t)/q
 // (the prod update is skipped for the last root or pair).  Each matrix product is one
-// CSR tile kernel whose epilogue applies the vector updates row by row, so a degree-d
-// polynomial costs d SpMV launches and no separate vector passes.  prod, t and y are in
-// the working precision (FP32 for the FP32/FP16/BF16 inner cycles), the matrix is the
-// inner cycle's stored copy.
+// SpMV kernel whose epilogue applies the vector updates row by row, so a degree-d
+// polynomial costs d SpMV launches and no separate vector passes.  The matrix is the
+// plan's SELL-32 copy in the inner storage precision; prod, t and y are in the working
+// precision (FP32 for the FP32/FP16/BF16 inner cycles).
 #pragma once
 
 #include "kernels.cuh"
@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(NT) k_poly_start(const SrcT* __restrict__ src,
 // y0 = 0 when `first`, else the current y.  in_cycle: also skip once the cycle ended.
 template <int P, int KIND>
 __global__ void __launch_bounds__(NT) k_poly_spmv(
-    const int* __restrict__ rp, const int* __restrict__ ci, const typename Tr<P>::S* __restrict__ av,
+    const int2* __restrict__ meta, const int* __restrict__ ci,
+    const typename Tr<P>::S* __restrict__ av, int nslices,
     int n, double a_scale, const typename Tr<P>::W* __restrict__ prod,
     const typename Tr<P>::W* __restrict__ tin, typename Tr<P>::W* __restrict__ y,
     typename Tr<P>::W* __restrict__ out, double c1d, double c2d, int first, const DevState* st,
@@ -60,11 +61,7 @@ __global__ void __launch_bounds__(NT) k_poly_spmv(
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int TR = SpmvSmem<P>::TR;
-  constexpr int CAP = SpmvSmem<P>::CAP;
   constexpr int RPT = TR / NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  W* prod_s = reinterpret_cast<W*>(smem_raw);
-  int* rp_s = reinterpret_cast<int*>(prod_s + CAP);
   __shared__ int s_skip;
   if (threadIdx.x == 0) s_skip = poly_skip(st, in_cycle);
   __syncthreads();
@@ -76,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_poly_spmv(
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int r0 = t * TR;
     W a[RPT];
-    tile_spmv<S, W, TR, CAP>(rp, ci, av, n, r0, rp_s, prod_s, xval, a);
+    sell_rows<S, W, RPT>(meta, ci, av, nslices, r0, xval, a);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int row = r0 + threadIdx.x + k * NT;

@@ -60,8 +60,12 @@ struct Plan {
   long long ld = 0;
   gmres_params p{};
   double a_scale = 1.0, v_scale = 1.0;
-  void* aval = nullptr;  // low-precision copy of A's values (A.vals itself for FP64)
-  bool own_aval = false;
+  // inner copy of A (SELL-32, storage precision)
+  int2* sell_meta = nullptr;   // per slice: offset of its first entry, width
+  int* sell_cols = nullptr;
+  void* sell_vals = nullptr;
+  int nslices = 0;
+  long long sell_nnz = 0;      // stored entries including padding
   void* V = nullptr;
   void *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;
   double *r = nullptr, *xb = nullptr, *bb = nullptr;
@@ -73,6 +77,7 @@ struct Plan {
   int hist_cap = 0;
   int sms = 148;
   int grid_spmv = 1, grid_vec = 1, grid_res = 1;
+  int tpw = 1;  // warp tiles per warp of the SpMV kernel
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -118,7 +123,6 @@ template <int P>
 static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  const size_t sm = sizeof(W) * SpmvSmem<P>::CAP + sizeof(int) * (SpmvSmem<P>::TR + 1) + 16;
   W* cur = (W*)pl.pa;
   W* nxt = (W*)pl.pb;
   W* y = (W*)pl.py;
@@ -129,18 +133,21 @@ static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
       if (op.last) {
         k_poly_axpy<P><<<pl.grid_elem, NT, 0, s>>>(cur, y, pl.n, op.c1, first, pl.st, in_cycle);
       } else {
-        k_poly_spmv<P, POLY_REAL><<<pl.grid_spmv, NT, sm, s>>>(
-            pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, nullptr, y, nxt,
+        k_poly_spmv<P, POLY_REAL><<<pl.grid_spmv, NT, 0, s>>>(
+            pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+            nullptr, y, nxt,
             op.c1, 0.0, first, pl.st, in_cycle);
         std::swap(cur, nxt);
       }
     } else {
-      k_poly_spmv<P, POLY_PAIR_A><<<pl.grid_spmv, NT, sm, s>>>(
-          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, nullptr, y,
+      k_poly_spmv<P, POLY_PAIR_A><<<pl.grid_spmv, NT, 0, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+          nullptr, y,
           op.last ? nullptr : t, op.c1, op.c2, first, pl.st, in_cycle);
       if (!op.last) {
-        k_poly_spmv<P, POLY_PAIR_B><<<pl.grid_spmv, NT, sm, s>>>(
-            pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.a_scale, cur, t, nullptr, nxt,
+        k_poly_spmv<P, POLY_PAIR_B><<<pl.grid_spmv, NT, 0, s>>>(
+            pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+            t, nullptr, nxt,
             op.c1, op.c2, 0, pl.st, in_cycle);
         std::swap(cur, nxt);
       }
@@ -162,7 +169,7 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   W* w3 = (W*)pl.w3;
   W* part = (W*)pl.part;
   if (which == 0) {
-    const size_t sm1 = SpmvSmem<P>::bytes(j + 2);
+    const size_t sm1 = SellSmem<P>::bytes(j + 2);
     if (!pl.poly.empty()) {
       if (j == 0)
         k_poly_start<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
@@ -171,20 +178,20 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
         k_poly_start<P, W><<<pl.grid_elem, NT, 0, s>>>(w3, pl.v_scale, pl.n, V, pl.ld, j,
                                                       (W*)pl.pa, pl.st);
       launch_poly<P>(pl, 1, s);
-      k_spmv_arnoldi<P, W, true><<<pl.grid_spmv, NT, sm1, s>>>(
-          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, pl.a_scale, (const W*)pl.py,
-          pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1);
+      k_spmv_sell<P, W, true><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, pl.a_scale,
+          (const W*)pl.py, pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1, pl.tpw);
       return;
     }
     const double rs = pl.a_scale / pl.v_scale;
     if (j == 0)
-      k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, sm1, s>>>(
-          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, pl.r, pl.v_scale, V, 0,
-          w1, part, pl.st, pl.arr.h1);
+      k_spmv_sell<P, double, false><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, pl.r,
+          pl.v_scale, V, 0, w1, part, pl.st, pl.arr.h1, pl.tpw);
     else
-      k_spmv_arnoldi<P, W><<<pl.grid_spmv, NT, sm1, s>>>(
-          pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, rs, w3, pl.v_scale, V, j, w1,
-          part, pl.st, pl.arr.h1);
+      k_spmv_sell<P, W, false><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, w3,
+          pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1, pl.tpw);
   } else if (which == 1) {
     k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
         V, pl.ld, j, pl.v_scale, w1, w2, part, pl.st, pl.arr.h1, pl.arr.h2);
@@ -212,7 +219,9 @@ static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   if (which == 0) {
-    k_lsq<<<1, 32, 0, s>>>(pl.st, pl.arr);
+    const int packed = pl.m <= LSQ_PACKED_MAX;
+    k_lsq<<<1, NT, packed ? sizeof(double) * (size_t)pl.m * (pl.m + 1) / 2 : 0, s>>>(pl.st, pl.arr,
+                                                                                   packed);
   } else if (which == 1) {
     if (!pl.poly.empty()) {
       k_vy<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
@@ -245,32 +254,35 @@ static int configure(Plan& pl) {
   constexpr int VEC = Tr<P>::VEC;
   // The attributes are per kernel, shared by every plan: set them for the largest restart
   // length so that a plan with a smaller m never lowers them under another plan.
-  const size_t sm_attr = SpmvSmem<P>::bytes(LSQ_MAX + 2);
-  const size_t sm_max = SpmvSmem<P>::bytes(pl.m + 2);
-  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t sm_attr = SellSmem<P>::bytes(LSQ_MAX + 2);
+  const size_t sm_max = SellSmem<P>::bytes(pl.m + 2);
+  CK(cudaFuncSetAttribute(k_spmv_sell<P, double, false>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_attr));
+  CK(cudaFuncSetAttribute(k_spmv_sell<P, W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_attr));
-  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CK(cudaFuncSetAttribute(k_spmv_sell<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_attr));
-  CK(cudaFuncSetAttribute(k_spmv_arnoldi<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_attr));
-  const size_t sm_poly = sizeof(W) * SpmvSmem<P>::CAP + sizeof(int) * (SpmvSmem<P>::TR + 1) + 16;
-  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_poly));
-  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_PAIR_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_poly));
-  CK(cudaFuncSetAttribute(k_poly_spmv<P, POLY_PAIR_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)sm_poly));
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
   CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(W) * (size_t)(LSQ_MAX + 1) * (1 + NWARP))));
+  CK(cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)(sizeof(double) * LSQ_PACKED_MAX * (LSQ_PACKED_MAX + 1) / 2)));
   pl.grid_elem = pl.sms * 8;
   int occ = 1;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_arnoldi<P, W>, NT, sm_max));
-  const long long ntiles = (pl.n + SpmvSmem<P>::TR - 1) / SpmvSmem<P>::TR;
-  pl.grid_spmv = (int)std::max(1LL, std::min(ntiles, (long long)std::max(occ, 1) * pl.sms));
+  // Work is split so that every warp (SpMV) or thread (CGS kernels) gets the same number
+  // of tiles or row groups, with at most two CTAs per SM: the cross-CTA reductions then
+  // sum about 2 x #SMs partials per column.
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_sell<P, W, false>, NT, sm_max));
+  const long long wt = SellSmem<P>::WT;
+  const long long nwt = (pl.n + wt - 1) / wt;
+  const long long spmv_warps = (long long)std::min(std::max(occ, 1), 2) * pl.sms * NWARP;
+  pl.tpw = (int)std::max(1LL, (nwt + spmv_warps - 1) / spmv_warps);
+  pl.grid_spmv = (int)std::max(1LL, (nwt + (long long)NWARP * pl.tpw - 1) / ((long long)NWARP * pl.tpw));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_u1<P>, NT, sm_u1));
-  const long long nblk = pl.ld / ((long long)NT * VEC);
-  pl.grid_vec = (int)std::max(1LL, std::min(nblk, (long long)std::max(occ, 1) * pl.sms));
+  const long long ngroups = pl.ld / VEC;
+  const long long vec_threads = (long long)std::min(std::max(occ, 1), 2) * pl.sms * NT;
+  const long long gpt = std::max(1LL, (ngroups + vec_threads - 1) / vec_threads);
+  pl.grid_vec = (int)std::max(1LL, (ngroups + (long long)NT * gpt - 1) / ((long long)NT * gpt));
   return GMRES_OK;
 }
 
@@ -278,7 +290,7 @@ static int configure_residual(Plan& pl) {
   int occ = 1;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual, NT, residual_smem()));
   const long long ntiles = (pl.n + RES_TR - 1) / RES_TR;
-  pl.grid_res = (int)std::max(1LL, std::min(ntiles, (long long)std::max(occ, 1) * pl.sms));
+  pl.grid_res = (int)std::max(1LL, std::min(ntiles, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
   return GMRES_OK;
 }
 
@@ -303,7 +315,9 @@ static void plan_free(Plan* pl) {
   if (pl->cap) cudaStreamDestroy(pl->cap);
   if (pl->ev0) cudaEventDestroy(pl->ev0);
   if (pl->ev1) cudaEventDestroy(pl->ev1);
-  if (pl->own_aval) cudaFree(pl->aval);
+  cudaFree(pl->sell_meta);
+  cudaFree(pl->sell_cols);
+  cudaFree(pl->sell_vals);
   cudaFree(pl->V);
   cudaFree(pl->w1);
   cudaFree(pl->w2);
@@ -412,35 +426,58 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   pl->arr.hist = q;
   if (cudaMallocHost((void**)&pl->h_st, sizeof(DevState)) != cudaSuccess) return fail(GMRES_ERR_OOM);
 
-  // Low-precision copy of A: values / s_A rounded to the storage type.
-  if (pl->prec == GMRES_FP64) {
-    pl->aval = (void*)A->vals;
-  } else {
-    if (pl->prec == GMRES_FP16 && A->nnz > 0) {
-      unsigned long long* d_mx = nullptr;
-      if (cudaMalloc((void**)&d_mx, 8) != cudaSuccess) return fail(GMRES_ERR_OOM);
-      cudaMemsetAsync(d_mx, 0, 8, s);
-      k_absmax<<<pl->sms * 4, 256, 0, s>>>(A->vals, A->nnz, d_mx);
-      unsigned long long bits = 0;
-      cudaMemcpyAsync(&bits, d_mx, 8, cudaMemcpyDeviceToHost, s);
-      if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) { cudaFree(d_mx); return fail(e_); }
-      cudaFree(d_mx);
-      double mx;
-      memcpy(&mx, &bits, 8);
-      if (!std::isfinite(mx)) return fail(GMRES_NONFINITE);
-      pl->a_scale = mx > 0.0 ? mx : 1.0;
-      pl->v_scale = std::sqrt((double)pl->n);
+  // Inner copy of A in SELL-32 (slices of 32 rows, column-major, padded to the slice's
+  // longest row): values / s_A rounded to the storage type (FP64 plans keep FP64 values).
+  if (pl->prec == GMRES_FP16 && A->nnz > 0) {
+    unsigned long long* d_mx = nullptr;
+    if (int e_ = CUDA_STATUS(cudaMalloc((void**)&d_mx, 8))) return fail(e_);
+    cudaMemsetAsync(d_mx, 0, 8, s);
+    k_absmax<<<pl->sms * 4, 256, 0, s>>>(A->vals, A->nnz, d_mx);
+    unsigned long long bits = 0;
+    cudaMemcpyAsync(&bits, d_mx, 8, cudaMemcpyDeviceToHost, s);
+    if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) { cudaFree(d_mx); return fail(e_); }
+    cudaFree(d_mx);
+    double mx;
+    memcpy(&mx, &bits, 8);
+    if (!std::isfinite(mx)) return fail(GMRES_NONFINITE);
+    pl->a_scale = mx > 0.0 ? mx : 1.0;
+    pl->v_scale = std::sqrt((double)pl->n);
+  }
+  {
+    std::vector<int> hrp((size_t)pl->n + 1);
+    if (int e_ = CUDA_STATUS(cudaMemcpyAsync(hrp.data(), A->row_ptr, sizeof(int) * hrp.size(),
+                                             cudaMemcpyDeviceToHost, s)))
+      return fail(e_);
+    if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
+    pl->nslices = (pl->n + 31) / 32;
+    std::vector<int2> meta(pl->nslices);
+    long long off = 0;
+    for (int sl = 0; sl < pl->nslices; ++sl) {
+      int w = 0;
+      for (int r = sl * 32; r < std::min(pl->n, sl * 32 + 32); ++r) w = std::max(w, hrp[r + 1] - hrp[r]);
+      meta[sl] = make_int2((int)off, w);
+      off += 32LL * w;
+      if (off >= (1LL << 31)) return fail(GMRES_ERR_TOO_LARGE);
     }
-    if ((e = alloc(&pl->aval, sb * (size_t)std::max(A->nnz, 1)))) return fail(e);
-    pl->own_aval = true;
+    pl->sell_nnz = off;
+    if ((e = alloc((void**)&pl->sell_meta, sizeof(int2) * meta.size()))) return fail(e);
+    if ((e = alloc((void**)&pl->sell_cols, sizeof(int) * (size_t)std::max(off, 1LL)))) return fail(e);
+    if ((e = alloc(&pl->sell_vals, sb * (size_t)std::max(off, 1LL)))) return fail(e);
+    if (int e_ = CUDA_STATUS(cudaMemcpyAsync(pl->sell_meta, meta.data(), sizeof(int2) * meta.size(),
+                                             cudaMemcpyHostToDevice, s)))
+      return fail(e_);
     const int blocks = pl->sms * 8;
-    if (pl->prec == GMRES_FP32)
-      k_cast_vals<float><<<blocks, 256, 0, s>>>(A->vals, (float*)pl->aval, A->nnz, pl->a_scale);
-    else if (pl->prec == GMRES_FP16)
-      k_cast_vals<__half><<<blocks, 256, 0, s>>>(A->vals, (__half*)pl->aval, A->nnz, pl->a_scale);
-    else
-      k_cast_vals<__nv_bfloat16><<<blocks, 256, 0, s>>>(A->vals, (__nv_bfloat16*)pl->aval, A->nnz,
-                                                        pl->a_scale);
+    const int* rp = A->row_ptr;
+    const int* ci = A->col_idx;
+    const double* va = A->vals;
+    dispatch(pl->prec, [&](auto PP) {
+      using S = typename Tr<decltype(PP)::value>::S;
+      k_build_sell<S><<<blocks, 256, 0, s>>>(rp, ci, va, pl->n, pl->sell_meta, pl->nslices,
+                                             pl->a_scale, pl->sell_cols, (S*)pl->sell_vals);
+      return 0;
+    });
+    // the meta upload reads `meta` asynchronously: finish before it goes out of scope
+    if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   }
   if ((e = dispatch(pl->prec, [&](auto P) { return configure<decltype(P)::value>(*pl); }))) return fail(e);
   if ((e = configure_residual(*pl))) return fail(e);
@@ -572,9 +609,10 @@ int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
     constexpr int P = decltype(PP)::value;
     using S = typename Tr<P>::S;
     using W = typename Tr<P>::W;
-    k_spmv_arnoldi<P, double><<<pl.grid_spmv, NT, SpmvSmem<P>::bytes(2), s>>>(
-        pl.A.row_ptr, pl.A.col_idx, (const S*)pl.aval, pl.n, pl.ld, pl.a_scale / pl.v_scale, v,
-        pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, (W*)pl.part, pl.st, pl.arr.h1);
+    k_spmv_sell<P, double, false><<<pl.grid_spmv, NT, SellSmem<P>::bytes(2), s>>>(
+        pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld,
+        pl.a_scale / pl.v_scale, v,
+        pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, (W*)pl.part, pl.st, pl.arr.h1, pl.tpw);
     return (int)cudaMemcpyAsync(y, pl.w1, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
   });
   if (e) return note_cuda((cudaError_t)e, __LINE__);
@@ -922,8 +960,8 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream) {
 // Some callers cannot call cudaMalloc: code whose device memory is owned by another
 // allocator that reserved the GPU up front, latency-critical loops that cannot afford
 // the implicit device synchronisation of cudaMalloc/cudaFree, and plug-ins that are not
-// allowed to allocate at all.  gmres_spmv_fp64_noalloc runs the same fused SpMV kernel
-// as gmres_plan_spmv on an FP64 plan, with its scratch (the kernel's device state,
+// allowed to allocate at all.  gmres_spmv_fp64_noalloc runs the CSR form of the fused
+// SpMV kernel behind gmres_plan_spmv (plans use a SELL-32 copy), with its scratch (the kernel's device state,
 // per-CTA partial sums and the basis column it writes) in the file-scope array below.
 // Every GPU that loads this library holds that array until the process exits.
 // ===========================================================================
