@@ -103,6 +103,8 @@ struct DevState {
   int zero_rhs;      // 1: ||b|| = 0, the answer is x = 0
   int hist_cap;      // capacity of the residual history
   long long iters;   // Arnoldi steps over the whole solve
+  long long iters0;  // Arnoldi steps before the current cycle
+  int last_step;     // last step whose second CGS kernel ran in this cycle (-1: none)
   long long max_iters;
   double rtol, inner_rtol;
   double bnorm, gamma, relres;
@@ -121,7 +123,7 @@ struct Arrays {
   double* R;     // (m+1) x m, column-major, after the Givens rotations
   double* cs;    // m
   double* sn;    // m
-  double* g;     // m+1   rotated right-hand side (g[0] = 1 at a cycle start)
+  double* gabs;  // m+1   |g_j| of the rotated right-hand side (|g_0| = 1 at a cycle start)
   double* y;     // m     least-squares solution
   double* hist;  // hist_cap relative residual estimates
 };

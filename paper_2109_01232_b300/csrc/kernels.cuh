@@ -31,6 +31,17 @@ namespace gm {
 
 __device__ __forceinline__ int read_flag(const int* p) { return *(volatile const int*)p; }
 
+// First unit of this CTA's (next == 0) or the next CTA's (next == 1) share when `units`
+// work units are split into equal contiguous ranges, each a multiple of `align` units
+// (the ranges of all CTAs differ by at most `align` units).  Every CTA of a grid gets
+// about the same work, so no SM waits on a second wave.
+__device__ __forceinline__ long long cta_begin(long long units, long long align, int next = 0) {
+  const long long chunks = units / align;
+  const long long b = blockIdx.x + next;
+  const long long c = chunks * b / gridDim.x;
+  return b >= gridDim.x ? units : c * align;
+}
+
 // ---------------------------------------------------------------------------
 // CSR tile engine: computes sum_p a[p] * xval(col[p]) for the rows
 // r0 + tid + k*NT (k < RPT) of one tile of TR rows.  The tile's nonzeros are
@@ -334,16 +345,142 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
   if (tid == 0) st->ticket[0] = 0;
 }
 
-// ---------------------------------------------------------------------------
-// Step kernel 1 on the SELL-32 copy, warp-independent form.  A warp owns "warp tiles" of
-// WT = 32 VEC consecutive rows (VEC slices): it stores its rows of V[:, j], computes its
-// rows of w = A v_j slice by slice, turns them from the slice layout (lane l holds rows
-// 32q + l) into the vector layout (lane l holds rows VEC l .. VEC l + VEC-1) through a
-// warp-private buffer, and accumulates the first-pass dot products over its rows.  There
-// is no CTA barrier inside the loop, so warps at different phases overlap.  Each warp
-// handles `tpw` consecutive warp tiles; the grid is sized so all warps get the same count.
-// Shared memory per warp: WT + (j+2) working values.
-// ---------------------------------------------------------------------------
+// ===========================================================================
+// The Arnoldi step on the SELL-32 copy, with no serial tails.
+//
+// Each step kernel ends by writing one partial sum per CTA and column -- no fence, no
+// ticket, no "last CTA".  The next kernel's CTAs all reduce those partials in their
+// prologue, in parallel and in the same fixed order, so every CTA holds bitwise the
+// same values:
+//   k_spmv_sell(j)  prologue (j > 0): the Givens update of step j-1 from ||w''||
+//                   (k_cgs_u2(j-1)'s partials) and ||A v_{j-1}|| (k_spmv_sell(j-1)'s);
+//                   every CTA computes it and takes the same stop decision, CTA 0 stores
+//                   it.  Body: v_j = store(sigma src), w = A v_j, partials of V_j^T w
+//                   and ||w||^2.
+//   k_cgs_u1(j)     prologue: h1 from the SpMV partials (CTA 0 stores h1).
+//                   Body: w' = w - V_j h1, partials of V_j^T w'.
+//   k_cgs_u2(j)     prologue: h2 (CTA 0 stores h2).  Body: w'' = w' - V_j h2, partials
+//                   of ||w''||^2.
+// k_finalize applies the update of the cycle's last step.  The SpMV partials are
+// double-buffered by step parity (k_spmv_sell(j+1) reads step j's norm column while its
+// CTAs write step j+1's partials).  The Givens update reads only data written by earlier
+// launches (h1, h2, earlier rotations, |g_j|), so the redundant computations agree.
+// ===========================================================================
+
+// Partial-sum buffers of one Arnoldi step (working type, column-major: column c of a
+// buffer with G CTAs is [c * G, c * G + G)).
+template <class W>
+struct StepParts {
+  W* p1[2];    // k_spmv_sell(j) writes p1[j & 1]: j+2 columns (dots, ||w||^2), g1 CTAs
+  W* p2;       // k_cgs_u1: j+1 columns, g2 CTAs
+  W* p3;       // k_cgs_u2: 1 column, g2 CTAs
+  int g1, g2;
+};
+
+// Column sums of per-CTA partials into shared memory: out[c] = sum_b part[c G + b].
+template <class W>
+__device__ __forceinline__ void cta_column_sums(const W* __restrict__ part, int ncol, int G, W* out) {
+  block_reduce_columns(part, ncol, G, [&](int c, W v) { out[c] = v; });
+}
+
+// CTA sum of the per-warp accumulators acc_w[c] (warp w's at acc0 + w * stride) written
+// as this CTA's partial of each column.
+template <class W>
+__device__ __forceinline__ void write_cta_partials(const W* acc0, int stride, int ncol, W* part) {
+  const int G = gridDim.x;
+  for (int c = threadIdx.x; c < ncol; c += NT) {
+    W s = W(0);
+    for (int w = 0; w < NWARP; ++w) s += acc0[(size_t)w * stride + c];
+    part[(long long)c * G + blockIdx.x] = s;
+  }
+}
+
+// Givens update of step js (Algorithm 1's least squares solved incrementally, FP64) with
+// the stop decision.  Called by every thread of the CTA; `sh` holds 3 (js + 2) + 2
+// doubles of shared memory.  Returns (through *done_out / *sigma_out, valid in all
+// threads after the call) whether the cycle ends and 1 / h_{js+1,js}.  If `writer`, the
+// CTA stores H[:, js], R[:, js], the rotation, |g_{js+1}|, the history and the flags.
+template <class W>
+__device__ void finalize_step(DevState* st, const Arrays& a, int js, const W* __restrict__ p3,
+                              int g3, const W* __restrict__ p1, int g1, bool writer, double* sh,
+                              int* done_out, double* sigma_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* col = sh;                 // js + 2
+  double* cs = sh + (js + 2);       // js
+  double* sn = cs + (js + 1);       // js
+  double* nrm = sn + (js + 1);      // [0] = ||w''||^2, [1] = ||A v_js||^2
+  const int ldh = st->m + 1;
+  if (warp == 0) {
+    const W v = warp_sum_partials(p3, g3);
+    if (lane == 0) nrm[0] = (double)v;
+  } else if (warp == 1) {
+    const W v = warp_sum_partials(p1 + (long long)(js + 1) * g1, g1);
+    if (lane == 0) nrm[1] = (double)v;
+  } else if (warp == 2) {
+    double* Hc = a.H + (long long)js * ldh;
+    for (int i = lane; i <= js; i += 32) {
+      const double h = a.h1[i] + a.h2[i];
+      col[i] = h;
+      if (writer) Hc[i] = h;
+    }
+  } else if (warp == 3) {
+    for (int i = lane; i < js; i += 32) {
+      cs[i] = a.cs[i];
+      sn[i] = a.sn[i];
+    }
+  }
+  __syncthreads();
+  __shared__ int s_done;
+  __shared__ double s_sigma;
+  if (tid == 0) {
+    const double hn = sqrt(nrm[0]), wnorm = sqrt(nrm[1]);
+    for (int i = 0; i < js; ++i) {
+      const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double x = col[js];
+    double c = 1.0, s = 0.0;
+    if (hn != 0.0) {
+      const double rho = hypot(x, hn);
+      c = x / rho;
+      s = hn / rho;
+    }
+    col[js] = c * x + s * hn;
+    col[js + 1] = 0.0;
+    const double res = a.gabs[js] * fabs(s);
+    const long long iters = st->iters0 + js + 1;
+    const bool bad = !isfinite(hn) || !isfinite(res) || !isfinite(col[js]);
+    const int brk = hn <= 16.0 * st->u_work * wnorm;
+    const int done = bad || brk || res <= st->stop_rel || js + 1 >= st->m || iters >= st->max_iters;
+    s_done = done;
+    s_sigma = brk ? 0.0 : 1.0 / hn;
+    if (writer) {
+      double* Hc = a.H + (long long)js * ldh;
+      double* Rc = a.R + (long long)js * ldh;
+      Hc[js + 1] = hn;
+      for (int i = 0; i <= js + 1; ++i) Rc[i] = col[i];
+      a.cs[js] = c;
+      a.sn[js] = s;
+      a.gabs[js + 1] = res;
+      st->k = js + 1;
+      st->iters = iters;
+      if (iters <= st->hist_cap)
+        a.hist[iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
+      st->breakdown = brk;
+      if (bad) {
+        st->status = ST_NONFINITE;
+        st->stop = 1;
+      }
+      if (done) st->cycle_done = 1;
+      st->sigma = s_sigma;
+    }
+  }
+  __syncthreads();
+  *done_out = s_done;
+  *sigma_out = s_sigma;
+}
+
 template <int P>
 struct SellSmem {
   using W = typename Tr<P>::W;
@@ -351,29 +488,49 @@ struct SellSmem {
   static size_t bytes(int ncol) { return sizeof(W) * (size_t)NWARP * (WT + ncol) + 16; }
 };
 
+// Step kernel 1 (see above).  A warp owns "warp tiles" of WT = 32 VEC consecutive rows
+// (VEC slices): it stores its rows of V[:, j], computes its rows of w = A v_j slice by
+// slice, turns them from the slice layout (lane l holds rows 32q + l) into the vector
+// layout (lane l holds rows VEC l .. VEC l + VEC-1) through a warp-private buffer, and
+// accumulates the first-pass dot products over its rows.  There is no CTA barrier inside
+// the loop, so warps at different phases overlap.  Each CTA owns an equal contiguous
+// range of warp tiles (cta_begin).  PLAIN: src is p(A) v_j (working type, unscaled),
+// gathered as is; V[:, j] was stored by the polynomial's first kernel.
 template <int P, class SrcT, bool PLAIN>
-__global__ void __launch_bounds__(NT) k_spmv_sell(
+__global__ void __launch_bounds__(NT, 2) k_spmv_sell(
     const int2* __restrict__ meta, const int* __restrict__ sc, const typename Tr<P>::S* __restrict__ sv,
     int nslices, int n, long long ld, double row_scale_d, const SrcT* __restrict__ src,
     double v_scale, typename Tr<P>::S* V, int j, typename Tr<P>::W* __restrict__ wout,
-    typename Tr<P>::W* __restrict__ part, DevState* st, double* __restrict__ h1, int tpw) {
+    StepParts<typename Tr<P>::W> parts, DevState* st, Arrays arr) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
   constexpr int WT = SellSmem<P>::WT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
   const int ncol = j + 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   W* ws = reinterpret_cast<W*>(smem_raw) + (size_t)warp * (WT + ncol);
   W* acc = ws + WT;
-  __shared__ int s_skip, s_last;
+  __shared__ int s_skip;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
   if (s_skip) return;
+  double sigma = 1.0;
+  if constexpr (!PLAIN) {  // with a polynomial, k_poly_start applied the update
+    if (j > 0) {
+      int done;
+      finalize_step(st, arr, j - 1, parts.p3, parts.g2, parts.p1[(j - 1) & 1], parts.g1,
+                    blockIdx.x == 0, gsh, &done, &sigma);
+      if (done) return;
+    } else {
+      sigma = st->sigma;
+    }
+  }
   for (int c = lane; c < ncol; c += 32) acc[c] = W(0);
   __syncwarp();
 
-  const SrcT f = (SrcT)(v_scale * st->sigma);
+  const SrcT f = (SrcT)(v_scale * sigma);
   const W row_scale = (W)row_scale_d;
   auto make = [&](SrcT x) -> S { return to_s<S>(f * x); };
   auto xval = [&](int c) -> W {
@@ -382,10 +539,8 @@ __global__ void __launch_bounds__(NT) k_spmv_sell(
   };
   S* Vj = V + (long long)j * ld;
   const int nwt = (n + WT - 1) / WT;
-  const int gw = blockIdx.x * NWARP + warp;
-  for (int t = 0; t < tpw; ++t) {
-    const int wt = gw * tpw + t;
-    if (wt >= nwt) break;
+  const int t1 = (int)cta_begin(nwt, 1, 1);
+  for (int wt = (int)cta_begin(nwt, 1) + warp; wt < t1; wt += NWARP) {
     const int r0 = wt * WT;
     const int s0 = r0 >> 5;
     int2 mt[VEC];
@@ -435,19 +590,7 @@ __global__ void __launch_bounds__(NT) k_spmv_sell(
     if (lane == 0) acc[j + 1] += nrm;
   }
   __syncthreads();
-  const int G = gridDim.x;
-  W* acc0 = reinterpret_cast<W*>(smem_raw) + WT;
-  for (int c = tid; c < ncol; c += NT) {
-    W s = W(0);
-    for (int w = 0; w < NWARP; ++w) s += acc0[(size_t)w * (WT + ncol) + c];
-    part[(long long)c * G + blockIdx.x] = s;
-  }
-  if (!arrive_last(&st->ticket[0], &s_last)) return;
-  block_reduce_columns(part, ncol, G, [&](int c, W s) {
-    if (c <= j) h1[c] = (double)s / v_scale;
-    else st->wnorm = sqrt((double)s);
-  });
-  if (tid == 0) st->ticket[0] = 0;
+  write_cta_partials(reinterpret_cast<W*>(smem_raw) + WT, WT + ncol, ncol, parts.p1[j & 1]);
 }
 
 // Store V[:, j] = store(v_scale * sigma * src) for all rows (the last basis vector of
@@ -463,17 +606,31 @@ __global__ void k_store_basis(const SrcT* __restrict__ src, double v_scale, int 
     Vj[i] = to_s<S>(f * src[i]);
 }
 
+// Prologue shared by the CGS kernels.  The partials hold dot products with the stored
+// (scaled) basis, so h[c] = (column sum) / v_scale is v_c . w; the update multiplies the
+// stored basis, so its coefficient is coef[c] = h[c] / v_scale.  CTA 0 stores h in FP64.
+template <class W>
+__device__ __forceinline__ void load_coefs(const W* __restrict__ part, int nc, int G, double v_scale,
+                                           W* coef, double* __restrict__ h) {
+  const bool writer = blockIdx.x == 0;
+  block_reduce_columns(part, nc, G, [&](int c, W v) {
+    const double hc = (double)v / v_scale;
+    coef[c] = (W)(hc / v_scale);
+    if (writer) h[c] = hc;
+  });
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
-// Step kernel 2: w' = w - V_j h1 (first pass update) and h2 = V_j^T w'.
+// Step kernel 2: h1 (prologue), w' = w - V_j h1, partials of V_j^T w'.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restrict__ V, long long ld,
+__global__ void __launch_bounds__(NT, 2) k_cgs_u1(const typename Tr<P>::S* __restrict__ V, long long ld,
                                                int j, double v_scale,
                                                const typename Tr<P>::W* __restrict__ win,
                                                typename Tr<P>::W* __restrict__ wout,
-                                               typename Tr<P>::W* __restrict__ part, DevState* st,
-                                               const double* __restrict__ h1,
-                                               double* __restrict__ h2) {
+                                               StepParts<typename Tr<P>::W> parts, DevState* st,
+                                               double* __restrict__ h1) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
@@ -481,16 +638,16 @@ __global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restri
   const int nc = j + 1;
   W* coef = reinterpret_cast<W*>(smem_raw);
   W* acc = coef + nc;
-  __shared__ int s_skip, s_last;
+  __shared__ int s_skip;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
   if (s_skip) return;
-  for (int c = tid; c < nc; c += NT) coef[c] = (W)(h1[c] / v_scale);
   for (int i = tid; i < NWARP * nc; i += NT) acc[i] = W(0);
-  __syncthreads();
+  load_coefs(parts.p1[j & 1], nc, parts.g1, v_scale, coef, h1);
   const long long ngroups = ld / VEC;
-  for (long long g = (long long)blockIdx.x * NT + tid; g < ngroups; g += (long long)gridDim.x * NT) {
+  const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
+  for (long long g = g0 + tid; g < g1; g += NT) {
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
@@ -499,93 +656,19 @@ __global__ void __launch_bounds__(NT) k_cgs_u1(const typename Tr<P>::S* __restri
     dots_to_acc<S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
   }
   __syncthreads();
-  const int G = gridDim.x;
-  for (int c = tid; c < nc; c += NT) {
-    W s = W(0);
-    for (int w = 0; w < NWARP; ++w) s += acc[w * nc + c];
-    part[(long long)c * G + blockIdx.x] = s;
-  }
-  if (!arrive_last(&st->ticket[1], &s_last)) return;
-  block_reduce_columns(part, nc, G, [&](int c, W s) { h2[c] = (double)s / v_scale; });
-  if (tid == 0) st->ticket[1] = 0;
-}
-
-// Givens update of column j (Algorithm 1's least-squares problem solved
-// incrementally, FP64).  Called by one whole warp: the lanes stage the new column
-// (h1 + h2, ||w''||) and the previous rotations in shared memory `sh` (3 (j+2) doubles)
-// with parallel loads, lane 0 applies the rotations and sets the cycle/solve flags,
-// and the lanes write the unrotated and rotated columns back.
-__device__ void givens_step_warp(DevState* st, const Arrays& a, int j, double hn, double* sh) {
-  const int lane = threadIdx.x & 31;
-  const int m = st->m;
-  const int ldh = m + 1;
-  double* col = sh;              // j+2 entries
-  double* cs = sh + (j + 2);     // j entries
-  double* sn = cs + (j + 1);     // j entries
-  for (int i = lane; i <= j; i += 32) {
-    col[i] = a.h1[i] + a.h2[i];
-    if (i < j) {
-      cs[i] = a.cs[i];
-      sn[i] = a.sn[i];
-    }
-  }
-  if (lane == 0) col[j + 1] = hn;
-  __syncwarp();
-  double* Hc = a.H + (long long)j * ldh;
-  for (int i = lane; i <= j + 1; i += 32) Hc[i] = col[i];
-  __syncwarp();
-  if (lane == 0) {
-    for (int i = 0; i < j; ++i) {
-      const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-      col[i] = t;
-    }
-    const double x = col[j], y = hn;
-    double c = 1.0, s = 0.0;
-    if (y != 0.0) {
-      const double rho = hypot(x, y);
-      c = x / rho;
-      s = y / rho;
-    }
-    col[j] = c * x + s * y;
-    col[j + 1] = 0.0;
-    a.cs[j] = c;
-    a.sn[j] = s;
-    const double gj = a.g[j];
-    a.g[j + 1] = -s * gj;
-    a.g[j] = c * gj;
-    const long long iters = st->iters + 1;
-    st->k = j + 1;
-    st->iters = iters;
-    const double res = fabs(s * gj);
-    if (iters <= st->hist_cap)
-      a.hist[iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
-    if (!isfinite(hn) || !isfinite(res) || !isfinite(col[j])) {
-      st->status = ST_NONFINITE;
-      st->stop = 1;
-      st->cycle_done = 1;
-    } else {
-      const int brk = hn <= 16.0 * st->u_work * st->wnorm;
-      st->breakdown = brk;
-      if (brk || res <= st->stop_rel || j + 1 >= m || iters >= st->max_iters) st->cycle_done = 1;
-      st->sigma = brk ? 0.0 : 1.0 / hn;
-    }
-  }
-  __syncwarp();
-  double* Rc = a.R + (long long)j * ldh;
-  for (int i = lane; i <= j + 1; i += 32) Rc[i] = col[i];
+  write_cta_partials(acc, nc, nc, parts.p2);
 }
 
 // ---------------------------------------------------------------------------
-// Step kernel 3: w'' = w' - V_j h2, ||w''||, then the Givens update.
+// Step kernel 3: h2 (prologue), w'' = w' - V_j h2, partials of ||w''||^2.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(NT) k_cgs_u2(const typename Tr<P>::S* __restrict__ V, long long ld,
+__global__ void __launch_bounds__(NT, 2) k_cgs_u2(const typename Tr<P>::S* __restrict__ V, long long ld,
                                                int j, double v_scale,
                                                const typename Tr<P>::W* __restrict__ win,
                                                typename Tr<P>::W* __restrict__ wout,
-                                               typename Tr<P>::W* __restrict__ part, DevState* st,
-                                               Arrays arr) {
+                                               StepParts<typename Tr<P>::W> parts, DevState* st,
+                                               double* __restrict__ h2) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
@@ -593,16 +676,16 @@ __global__ void __launch_bounds__(NT) k_cgs_u2(const typename Tr<P>::S* __restri
   const int nc = j + 1;
   W* coef = reinterpret_cast<W*>(smem_raw);
   __shared__ W accw[NWARP];
-  __shared__ int s_skip, s_last;
+  __shared__ int s_skip;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
   if (s_skip) return;
-  for (int c = tid; c < nc; c += NT) coef[c] = (W)(arr.h2[c] / v_scale);
-  __syncthreads();
+  load_coefs(parts.p2, nc, parts.g2, v_scale, coef, h2);
   W nrm = W(0);
   const long long ngroups = ld / VEC;
-  for (long long g = (long long)blockIdx.x * NT + tid; g < ngroups; g += (long long)gridDim.x * NT) {
+  const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
+  for (long long g = g0 + tid; g < g1; g += NT) {
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
@@ -614,39 +697,42 @@ __global__ void __launch_bounds__(NT) k_cgs_u2(const typename Tr<P>::S* __restri
   nrm = warp_sum(nrm);
   if (lane == 0) accw[warp] = nrm;
   __syncthreads();
-  const int G = gridDim.x;
   if (tid == 0) {
     W s = W(0);
     for (int w = 0; w < NWARP; ++w) s += accw[w];
-    part[blockIdx.x] = s;
+    parts.p3[blockIdx.x] = s;
+    if (blockIdx.x == 0) st->last_step = j;
   }
-  if (!arrive_last(&st->ticket[2], &s_last)) return;
-  if (warp == 0) {
-    __shared__ double gsh[3 * (LSQ_MAX + 2)];
-    W s0 = W(0), s1 = W(0), s2 = W(0), s3 = W(0);
-    int b = lane;
-    for (; b + 96 < G; b += 128) {
-      s0 += __ldcg(&part[b]);
-      s1 += __ldcg(&part[b + 32]);
-      s2 += __ldcg(&part[b + 64]);
-      s3 += __ldcg(&part[b + 96]);
-    }
-    for (; b < G; b += 32) s0 += __ldcg(&part[b]);
-    const W s = warp_sum((s0 + s1) + (s2 + s3));
-    if (lane == 0) st->ticket[2] = 0;
-    givens_step_warp(st, arr, j, sqrt((double)s), gsh);
+}
+
+// Applies the pending Givens update of the cycle's last step (one CTA).
+template <int P>
+__global__ void __launch_bounds__(NT) k_finalize(StepParts<typename Tr<P>::W> parts, DevState* st,
+                                                 Arrays arr) {
+  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
+  __shared__ int s_go, s_js;
+  if (threadIdx.x == 0) {
+    s_js = st->last_step;
+    s_go = !read_flag(&st->stop) && s_js >= 0 && st->k == s_js;
   }
+  __syncthreads();
+  if (!s_go) return;
+  int done;
+  double sigma;
+  finalize_step(st, arr, s_js, parts.p3, parts.g2, parts.p1[s_js & 1], parts.g1, true, gsh, &done,
+                &sigma);
 }
 
 // ---------------------------------------------------------------------------
 // End of a cycle: least squares R y = g by back substitution (FP64, one warp solves).
-// A trailing diagonal entry below 16 u max|R| is dropped (singular factor).
-// R is staged in shared memory (packed upper triangle, column by column) when
-// `packed` is set (m <= LSQ_PACKED_MAX); the loads are spread over all threads.
+// g is rebuilt from the rotations (g_0 = 1).  A trailing diagonal entry below
+// 16 u max|R| is dropped (singular factor).  R is staged in shared memory (packed upper
+// triangle, column by column) when `packed` is set (m <= LSQ_PACKED_MAX).
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Rs = reinterpret_cast<double*>(smem_raw);
-  __shared__ double gw[LSQ_MAX];
+  __shared__ double gw[LSQ_MAX + 1];
   __shared__ double red[NWARP];
   __shared__ int s_kk, s_skip;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -664,9 +750,13 @@ __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) 
     }
   rmax = warp_max(rmax);
   if (lane == 0) red[warp] = rmax;
-  for (int i = tid; i < k; i += NT) gw[i] = a.g[i];
   __syncthreads();
   if (tid == 0) {
+    double g = 1.0;  // g_0 = 1 (unit least-squares right-hand side)
+    for (int i = 0; i < k; ++i) {
+      gw[i] = a.cs[i] * g;
+      g = -a.sn[i] * g;
+    }
     double mx = 0.0;
     for (int w = 0; w < NWARP; ++w) mx = fmax(mx, red[w]);
     int kk = k;
@@ -718,7 +808,8 @@ __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict
   for (int c = tid; c < kk; c += NT) coef[c] = (W)y[c];
   __syncthreads();
   const long long ngroups = ld / VEC;
-  for (long long g = (long long)blockIdx.x * NT + tid; g < ngroups; g += (long long)gridDim.x * NT) {
+  const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
+  for (long long g = g0 + tid; g < g1; g += NT) {
     const long long base = g * VEC;
     W u[VEC];
 #pragma unroll
@@ -819,8 +910,10 @@ __global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, con
       st->status = status;
       if (!stop) {
         st->sigma = 1.0 / gamma;
-        arr.g[0] = 1.0;
+        arr.gabs[0] = 1.0;
         st->k = 0;
+        st->last_step = -1;
+        st->iters0 = st->iters;
         st->cycle_done = 0;
         st->breakdown = 0;
         st->stop_rel = st->mode == 0 ? st->rtol * bnorm / gamma

@@ -22,20 +22,31 @@ __device__ __forceinline__ int poly_skip(const DevState* st, int in_cycle) {
   return read_flag(&st->stop) | (in_cycle ? read_flag(&st->cycle_done) : 0);
 }
 
-// First kernel of p(A) v_j inside an Arnoldi step: V[:, j] = store(v_scale * sigma * src)
-// (the normalisation of the previous step) and prod = v_j in the working type.
+// First kernel of p(A) v_j inside an Arnoldi step.  For j > 0 it first applies the
+// Givens update of step j-1 (every CTA computes it, CTA 0 stores it: see k_spmv_sell),
+// which gives 1 / h_{j,j-1}; then V[:, j] = store(v_scale * sigma * src) (the
+// normalisation of the previous step) and prod = v_j in the working type.
 template <int P, class SrcT>
 __global__ void __launch_bounds__(NT) k_poly_start(const SrcT* __restrict__ src, double v_scale,
                                                    int n, typename Tr<P>::S* V, long long ld,
                                                    int j, typename Tr<P>::W* __restrict__ prod,
-                                                   const DevState* st) {
+                                                   StepParts<typename Tr<P>::W> parts,
+                                                   DevState* st, Arrays arr) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
+  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
   __shared__ int s_skip;
   if (threadIdx.x == 0) s_skip = poly_skip(st, 1);
   __syncthreads();
   if (s_skip) return;
-  const SrcT f = (SrcT)(v_scale * st->sigma);
+  double sigma = st->sigma;
+  if (j > 0) {
+    int done;
+    finalize_step(st, arr, j - 1, parts.p3, parts.g2, parts.p1[(j - 1) & 1], parts.g1,
+                  blockIdx.x == 0, gsh, &done, &sigma);
+    if (done) return;
+  }
+  const SrcT f = (SrcT)(v_scale * sigma);
   const W inv = (W)(1.0 / v_scale);
   S* Vj = V + (long long)j * ld;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
@@ -133,7 +144,8 @@ __global__ void __launch_bounds__(NT) k_vy(const typename Tr<P>::S* __restrict__
   __syncthreads();
   const W inv = (W)(1.0 / v_scale);
   const long long ngroups = ld / VEC;
-  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < ngroups; g += (long long)gridDim.x * NT) {
+  const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
+  for (long long g = g0 + threadIdx.x; g < g1; g += NT) {
     const long long base = g * VEC;
     W acc[VEC];
 #pragma unroll

@@ -69,7 +69,8 @@ struct Plan {
   void* V = nullptr;
   void *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;
   double *r = nullptr, *xb = nullptr, *bb = nullptr;
-  void* part = nullptr;
+  void* part = nullptr;  // per-CTA partial sums: residual, then the step buffers
+  size_t part_step_off = 0;
   DevState* st = nullptr;
   DevState* h_st = nullptr;  // pinned
   double* arr_mem = nullptr;
@@ -77,7 +78,6 @@ struct Plan {
   int hist_cap = 0;
   int sms = 148;
   int grid_spmv = 1, grid_vec = 1, grid_res = 1;
-  int tpw = 1;  // warp tiles per warp of the SpMV kernel
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -117,6 +117,22 @@ static std::vector<PolyOp> poly_program(const std::vector<double>& re, const std
 // ---------------------------------------------------------------------------
 // Kernel launch sequences (templated on the storage precision).
 // ---------------------------------------------------------------------------
+
+// Partial-sum buffers of the Arnoldi step kernels (inside pl.part, after the residual's).
+template <int P>
+static StepParts<typename Tr<P>::W> step_parts(const Plan& pl) {
+  using W = typename Tr<P>::W;
+  StepParts<W> sp;
+  W* base = reinterpret_cast<W*>(static_cast<unsigned char*>(pl.part) + pl.part_step_off);
+  const size_t n1 = (size_t)(pl.m + 2) * pl.grid_spmv;
+  sp.p1[0] = base;
+  sp.p1[1] = base + n1;
+  sp.p2 = base + 2 * n1;
+  sp.p3 = sp.p2 + (size_t)(pl.m + 1) * pl.grid_vec;
+  sp.g1 = pl.grid_spmv;
+  sp.g2 = pl.grid_vec;
+  return sp;
+}
 
 // y = p(A) prod0 (prod0 is pl.pa, overwritten; pl.pb / pl.pt are scratch).
 template <int P>
@@ -167,37 +183,37 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   W* w1 = (W*)pl.w1;
   W* w2 = (W*)pl.w2;
   W* w3 = (W*)pl.w3;
-  W* part = (W*)pl.part;
+  const StepParts<W> sp = step_parts<P>(pl);
   if (which == 0) {
     const size_t sm1 = SellSmem<P>::bytes(j + 2);
     if (!pl.poly.empty()) {
       if (j == 0)
         k_poly_start<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
-                                                           (W*)pl.pa, pl.st);
+                                                           (W*)pl.pa, sp, pl.st, pl.arr);
       else
         k_poly_start<P, W><<<pl.grid_elem, NT, 0, s>>>(w3, pl.v_scale, pl.n, V, pl.ld, j,
-                                                      (W*)pl.pa, pl.st);
+                                                      (W*)pl.pa, sp, pl.st, pl.arr);
       launch_poly<P>(pl, 1, s);
       k_spmv_sell<P, W, true><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, pl.a_scale,
-          (const W*)pl.py, pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1, pl.tpw);
+          (const W*)pl.py, pl.v_scale, V, j, w1, sp, pl.st, pl.arr);
       return;
     }
     const double rs = pl.a_scale / pl.v_scale;
     if (j == 0)
       k_spmv_sell<P, double, false><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, pl.r,
-          pl.v_scale, V, 0, w1, part, pl.st, pl.arr.h1, pl.tpw);
+          pl.v_scale, V, 0, w1, sp, pl.st, pl.arr);
     else
       k_spmv_sell<P, W, false><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, w3,
-          pl.v_scale, V, j, w1, part, pl.st, pl.arr.h1, pl.tpw);
+          pl.v_scale, V, j, w1, sp, pl.st, pl.arr);
   } else if (which == 1) {
     k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
-        V, pl.ld, j, pl.v_scale, w1, w2, part, pl.st, pl.arr.h1, pl.arr.h2);
+        V, pl.ld, j, pl.v_scale, w1, w2, sp, pl.st, pl.arr.h1);
   } else {
     k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1), s>>>(V, pl.ld, j, pl.v_scale, w2,
-                                                                     w3, part, pl.st, pl.arr);
+                                                                     w3, sp, pl.st, pl.arr.h2);
   }
 }
 
@@ -219,6 +235,7 @@ static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   if (which == 0) {
+    k_finalize<P><<<1, NT, 0, s>>>(step_parts<P>(pl), pl.st, pl.arr);
     const int packed = pl.m <= LSQ_PACKED_MAX;
     k_lsq<<<1, NT, packed ? sizeof(double) * (size_t)pl.m * (pl.m + 1) / 2 : 0, s>>>(pl.st, pl.arr,
                                                                                    packed);
@@ -269,20 +286,15 @@ static int configure(Plan& pl) {
                           (int)(sizeof(double) * LSQ_PACKED_MAX * (LSQ_PACKED_MAX + 1) / 2)));
   pl.grid_elem = pl.sms * 8;
   int occ = 1;
-  // Work is split so that every warp (SpMV) or thread (CGS kernels) gets the same number
-  // of tiles or row groups, with at most two CTAs per SM: the cross-CTA reductions then
-  // sum about 2 x #SMs partials per column.
+  // At most two CTAs per SM, each with an equal contiguous share of the rows (the kernels
+  // split the work with cta_begin): no second wave, and the cross-CTA reductions sum about
+  // 2 x #SMs partials per column.
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_sell<P, W, false>, NT, sm_max));
-  const long long wt = SellSmem<P>::WT;
-  const long long nwt = (pl.n + wt - 1) / wt;
-  const long long spmv_warps = (long long)std::min(std::max(occ, 1), 2) * pl.sms * NWARP;
-  pl.tpw = (int)std::max(1LL, (nwt + spmv_warps - 1) / spmv_warps);
-  pl.grid_spmv = (int)std::max(1LL, (nwt + (long long)NWARP * pl.tpw - 1) / ((long long)NWARP * pl.tpw));
+  const long long nwt = (pl.n + SellSmem<P>::WT - 1) / SellSmem<P>::WT;
+  pl.grid_spmv = (int)std::max(1LL, std::min(nwt, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_u1<P>, NT, sm_u1));
-  const long long ngroups = pl.ld / VEC;
-  const long long vec_threads = (long long)std::min(std::max(occ, 1), 2) * pl.sms * NT;
-  const long long gpt = std::max(1LL, (ngroups + vec_threads - 1) / vec_threads);
-  pl.grid_vec = (int)std::max(1LL, (ngroups + (long long)NT * gpt - 1) / ((long long)NT * gpt));
+  const long long nchunks = pl.ld / VEC / 32;  // 32-group chunks (one warp's worth)
+  pl.grid_vec = (int)std::max(1LL, std::min(nchunks, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
   return GMRES_OK;
 }
 
@@ -421,7 +433,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   pl->arr.R = q; q += (m + 1) * m;
   pl->arr.cs = q; q += m;
   pl->arr.sn = q; q += m;
-  pl->arr.g = q; q += m + 1;
+  pl->arr.gabs = q; q += m + 1;
   pl->arr.y = q; q += m;
   pl->arr.hist = q;
   if (cudaMallocHost((void**)&pl->h_st, sizeof(DevState)) != cudaSuccess) return fail(GMRES_ERR_OOM);
@@ -481,8 +493,9 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   }
   if ((e = dispatch(pl->prec, [&](auto P) { return configure<decltype(P)::value>(*pl); }))) return fail(e);
   if ((e = configure_residual(*pl))) return fail(e);
-  const int gmax = std::max({pl->grid_spmv, pl->grid_vec, pl->grid_res});
-  if ((e = alloc(&pl->part, 8 * (size_t)(m + 2) * gmax))) return fail(e);
+  pl->part_step_off = 8 * (size_t)(2 * pl->grid_res + 2);
+  const size_t step_parts_n = 2 * (size_t)(m + 2) * pl->grid_spmv + (size_t)(m + 2) * pl->grid_vec;
+  if ((e = alloc(&pl->part, pl->part_step_off + 8 * step_parts_n))) return fail(e);
   cudaEventRecord(t1, s);
   if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   float ms = 0.f;
@@ -612,7 +625,7 @@ int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
     k_spmv_sell<P, double, false><<<pl.grid_spmv, NT, SellSmem<P>::bytes(2), s>>>(
         pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld,
         pl.a_scale / pl.v_scale, v,
-        pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, (W*)pl.part, pl.st, pl.arr.h1, pl.tpw);
+        pl.v_scale, (S*)pl.V, 0, (W*)pl.w1, step_parts<P>(pl), pl.st, pl.arr);
     return (int)cudaMemcpyAsync(y, pl.w1, sizeof(W) * (size_t)pl.n, cudaMemcpyDeviceToDevice, s);
   });
   if (e) return note_cuda((cudaError_t)e, __LINE__);
@@ -632,12 +645,13 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(pl.bb, v0, nb, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(pl.xb, 0, nb, s));
-  launch_residual(pl, 1, s);  // r = v0, sigma = 1/||v0||, g[0] = 1
+  launch_residual(pl, 1, s);  // r = v0, sigma = 1/||v0||, |g_0| = 1
   int e = dispatch(pl.prec, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using S = typename Tr<P>::S;
     using W = typename Tr<P>::W;
     for (int j = 0; j < steps; ++j) launch_step<P>(pl, j, s);
+    k_finalize<P><<<1, NT, 0, s>>>(step_parts<P>(pl), pl.st, pl.arr);
     k_store_basis<P, W><<<pl.sms * 4, 256, 0, s>>>((const W*)pl.w3, pl.v_scale, pl.n, (S*)pl.V, pl.ld,
                                                    steps, pl.st);
     return (int)cudaGetLastError();
