@@ -49,7 +49,9 @@ typedef enum {
   GMRES_ERR_INVALID = 4,     /* bad argument (null pointer, size, parameter, CSR structure) */
   GMRES_ERR_OOM = 5,         /* device allocation failed */
   GMRES_ERR_CUDA = 6,        /* any other CUDA runtime error */
-  GMRES_ERR_TOO_LARGE = 7    /* a size exceeds a documented maximum */
+  GMRES_ERR_TOO_LARGE = 7,   /* a size exceeds a documented maximum */
+  GMRES_ERR_DEVICE_TIMEOUT = 8 /* a kernel's bounded wait on its own copies expired (the kernel
+                                  stopped and reported instead of waiting further) */
 } gmres_status;
 
 /* Storage precision of the inner solve: the Krylov basis V and the copy of A
@@ -79,7 +81,18 @@ typedef struct {
   int32_t poly_degree;      /* degree d of the GMRES polynomial preconditioner; 0 = none */
   uint64_t seed;            /* SplitMix64 seed of the polynomial's start vector */
   int32_t record_history;   /* nonzero: keep |g_{j+1}| per iteration in gmres_stats */
+  int32_t cgs_kernel;       /* gmres_cgs_kernel: how the CGS2 update kernels read V */
 } gmres_params;
+
+/* Forms of the two CGS2 update kernels (the same arithmetic per row; both produce the
+ * same partial-sum layout for the next kernel). */
+typedef enum {
+  GMRES_CGS_REGISTER = 0,  /* vector loads into registers (default: the faster form on a
+                              B300 at every step length measured) */
+  GMRES_CGS_TMA = 1        /* cp.async.bulk copies into a shared-memory ring, one producer
+                              warp; used for the steps whose basis block fits two stages,
+                              the register form for the others */
+} gmres_cgs_kernel;
 
 #define GMRES_MAX_RESTART 512
 #define GMRES_MAX_POLY_DEGREE 96

@@ -18,9 +18,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgmres_ir.so")
 
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+CGS_KERNEL = {"register": 0, "tma": 1}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: "ERR_INVALID",
-          5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TOO_LARGE"}
-OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TOO_LARGE = range(8)
+          5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TOO_LARGE", 8: "ERR_DEVICE_TIMEOUT"}
+(OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TOO_LARGE,
+ ERR_DEVICE_TIMEOUT) = range(9)
 MAX_RESTART = 512
 MAX_POLY_DEGREE = 96
 
@@ -40,7 +42,8 @@ class params_t(ctypes.Structure):
     _fields_ = [("restart_m", ctypes.c_int32), ("rtol", ctypes.c_double),
                 ("inner_rtol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("inner_prec", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32),
+                ("cgs_kernel", ctypes.c_int32)]
 
 
 class stats_t(ctypes.Structure):
@@ -136,6 +139,8 @@ def default_params(**kw) -> params_t:
     for k, v in kw.items():
         if k == "inner_prec" and isinstance(v, str):
             v = PREC[v]
+        if k == "cgs_kernel" and isinstance(v, str):
+            v = CGS_KERNEL[v]
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k}")
         setattr(p, k, v)

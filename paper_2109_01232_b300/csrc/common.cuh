@@ -71,6 +71,34 @@ __device__ __forceinline__ void ldv_stream(const T* __restrict__ p, T (&o)[N]) {
   memcpy(o, u, sizeof(u));
 }
 
+// L2 evict-first loads for data that the kernel reads for the last time before other
+// data needs the cache (the basis V streams through L2 once per pass, and marking it
+// keeps the matrix and the work vectors resident).  Only for memory that no thread
+// writes during the kernel: the asm is not ordered against other memory operations.
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+template <class T, int N>
+__device__ __forceinline__ void ldv_evict_first(const T* __restrict__ p, T (&o)[N]) {
+  constexpr int Q = (int)(sizeof(T) * N / 16);
+  const unsigned long long pol = l2_evict_first_policy();
+  uint4 u[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    asm("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(u[q].x), "=r"(u[q].y), "=r"(u[q].z), "=r"(u[q].w)
+        : "l"(reinterpret_cast<const uint4*>(p) + q), "l"(pol));
+  memcpy(o, u, sizeof(u));
+}
+// ldv (EF = false) or ldv_evict_first (EF = true).
+template <bool EF, class T, int N>
+__device__ __forceinline__ void ldv_sel(const T* __restrict__ p, T (&o)[N]) {
+  if constexpr (EF) ldv_evict_first(p, o);
+  else ldv(p, o);
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -85,7 +113,8 @@ __device__ __forceinline__ T warp_max(T v) {
 }
 
 // Status codes (mirrors gmres_status in include/gmres_ir.h).
-enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3, ST_INVALID = 4 };
+enum { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3, ST_INVALID = 4,
+       ST_TIMEOUT = 8 };
 
 // Device-resident state of one solve.  The host writes it once before a solve and
 // reads it once after; every decision in between is taken on the device.

@@ -25,6 +25,8 @@
 // same length ld and zero padding, so vector loads never need a tail.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace gm {
@@ -152,26 +154,26 @@ __device__ __forceinline__ W warp_sum_partials(const W* __restrict__ p, int G) {
   return warp_sum((s0 + s1) + (s2 + s3));
 }
 
-// Reduces ncol columns of per-CTA partials part[c * G + b] with the whole CTA and calls
-// out(c, sum) once per column (lane 0 of the warp that owns it).  Warp w owns columns
-// w, w + NWARP, ...; each lane keeps four columns' loads in flight.  Fixed order.
-template <class W, class F>
+// Reduces ncol columns of per-CTA partials part[c * G + b] with the CTA's first NW warps
+// and calls out(c, sum) once per column (lane 0 of the warp that owns it).  Warp w owns
+// columns w, w + NW, ...; each lane keeps four columns' loads in flight.  Fixed order.
+template <int NW = NWARP, class W, class F>
 __device__ __forceinline__ void block_reduce_columns(const W* __restrict__ part, int ncol, int G,
                                                      const F& out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c0 = warp; c0 < ncol; c0 += 4 * NWARP) {
+  for (int c0 = warp; c0 < ncol; c0 += 4 * NW) {
     W s[4] = {W(0), W(0), W(0), W(0)};
 #pragma unroll 4
     for (int b = lane; b < G; b += 32) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int c = c0 + q * NWARP;
+        const int c = c0 + q * NW;
         if (c < ncol) s[q] += __ldcg(&part[(long long)c * G + b]);
       }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int c = c0 + q * NWARP;
+      const int c = c0 + q * NW;
       const W v = warp_sum(s[q]);
       if (c < ncol && lane == 0) out(c, v);
     }
@@ -179,13 +181,14 @@ __device__ __forceinline__ void block_reduce_columns(const W* __restrict__ part,
 }
 
 // w[q] -= sum_{b < B} coef[c0 + b] * V[c0 + b][base + q]: the B column vectors are loaded
-// before any is used, so B 16-byte loads per thread are in flight.
-template <int B, class S, class W, int VEC>
+// before any is used, so B 16-byte loads per thread are in flight.  EF: the last read of
+// these columns in this kernel (L2 evict-first loads, see ldv_evict_first).
+template <int B, bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void update_cols(const S* __restrict__ V, long long ld, long long base,
                                             int c0, const W* __restrict__ coef, W (&wv)[VEC]) {
   S v[B][VEC];
 #pragma unroll
-  for (int b = 0; b < B; ++b) ldv(V + (long long)(c0 + b) * ld + base, v[b]);
+  for (int b = 0; b < B; ++b) ldv_sel<EF>(V + (long long)(c0 + b) * ld + base, v[b]);
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const W k = coef[c0 + b];
@@ -195,12 +198,12 @@ __device__ __forceinline__ void update_cols(const S* __restrict__ V, long long l
 }
 
 // d[b] = sum_q V[c0 + b][base + q] * w[q] for b < B (B loads in flight).
-template <int B, class S, class W, int VEC>
+template <int B, bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void dot_cols(const S* __restrict__ V, long long ld, long long base, int c0,
                                          const W (&wv)[VEC], W (&d)[B]) {
   S v[B][VEC];
 #pragma unroll
-  for (int b = 0; b < B; ++b) ldv(V + (long long)(c0 + b) * ld + base, v[b]);
+  for (int b = 0; b < B; ++b) ldv_sel<EF>(V + (long long)(c0 + b) * ld + base, v[b]);
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     W t = W(0);
@@ -210,16 +213,16 @@ __device__ __forceinline__ void dot_cols(const S* __restrict__ V, long long ld, 
   }
 }
 
-// Dot products of w with the nc columns V[0..nc) for this thread's rows, summed over the
-// warp and added to acc[warp * stride + c] by lane 0.
-template <class S, class W, int VEC>
+// Dot products of w with the columns V[c0..nc) for this thread's rows, summed over the
+// warp and added to acc[c] by lane 0.  EF: see update_cols.
+template <bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long ld, long long base,
-                                            int nc, const W (&wv)[VEC], W* acc) {
+                                            int nc, const W (&wv)[VEC], W* acc, int c0 = 0) {
   const int lane = threadIdx.x & 31;
-  int c = 0;
+  int c = c0;
   for (; c + 8 <= nc; c += 8) {
     W d[8];
-    dot_cols<8>(V, ld, base, c, wv, d);
+    dot_cols<8, EF>(V, ld, base, c, wv, d);
 #pragma unroll
     for (int b = 0; b < 8; ++b) d[b] = warp_sum(d[b]);
     if (lane == 0) {
@@ -229,19 +232,19 @@ __device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long l
   }
   for (; c < nc; ++c) {
     W d[1];
-    dot_cols<1>(V, ld, base, c, wv, d);
+    dot_cols<1, EF>(V, ld, base, c, wv, d);
     const W t = warp_sum(d[0]);
     if (lane == 0) acc[c] += t;
   }
 }
 
-// w -= V[0..nc) coef for this thread's rows.
-template <class S, class W, int VEC>
+// w -= V[0..nc) coef for this thread's rows.  EF: see update_cols.
+template <bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void update_all(const S* __restrict__ V, long long ld, long long base,
                                            int nc, const W* __restrict__ coef, W (&wv)[VEC]) {
   int c = 0;
-  for (; c + 8 <= nc; c += 8) update_cols<8>(V, ld, base, c, coef, wv);
-  for (; c < nc; ++c) update_cols<1>(V, ld, base, c, coef, wv);
+  for (; c + 8 <= nc; c += 8) update_cols<8, EF>(V, ld, base, c, coef, wv);
+  for (; c < nc; ++c) update_cols<1, EF>(V, ld, base, c, coef, wv);
 }
 
 template <int P>
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     W nrm = W(0);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
-    dots_to_acc<S, W, VEC>(V, ld, gb, j + 1, wv, acc + warp * ncol);
+    dots_to_acc<false, S, W, VEC>(V, ld, gb, j + 1, wv, acc + warp * ncol);
     nrm = warp_sum(nrm);
     if (lane == 0) acc[warp * ncol + j + 1] += nrm;
     __syncthreads();
@@ -349,9 +352,10 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
 // The Arnoldi step on the SELL-32 copy, with no serial tails.
 //
 // Each step kernel ends by writing one partial sum per CTA and column -- no fence, no
-// ticket, no "last CTA".  The next kernel's CTAs all reduce those partials in their
-// prologue, in parallel and in the same fixed order, so every CTA holds bitwise the
-// same values:
+// ticket, no "last CTA".  The next kernel reduces those partials in its prologue: each
+// cluster of CL CTAs splits the columns among its CTAs and shares the sums through
+// distributed shared memory (cluster_column_sums), always in the same fixed order, so
+// every CTA holds bitwise the same values:
 //   k_spmv_sell(j)  prologue (j > 0): the Givens update of step j-1 from ||w''||
 //                   (k_cgs_u2(j-1)'s partials) and ||A v_{j-1}|| (k_spmv_sell(j-1)'s);
 //                   every CTA computes it and takes the same stop decision, CTA 0 stores
@@ -365,6 +369,15 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
 // double-buffered by step parity (k_spmv_sell(j+1) reads step j's norm column while its
 // CTAs write step j+1's partials).  The Givens update reads only data written by earlier
 // launches (h1, h2, earlier rotations, |g_j|), so the redundant computations agree.
+//
+// Row order.  Each kernel of a step streams all j+1 basis columns, more than the L2 holds
+// once j is large, and LRU keeps what a kernel touched last.  Consecutive step kernels
+// therefore walk their CTA's rows in opposite directions (k_spmv_sell forward for even j,
+// k_cgs_u1 the other way, k_cgs_u2 like k_spmv_sell), so each starts on the rows whose
+// basis entries the previous kernel left in L2.  The SpMV's dot products read the old
+// columns evict-first (ldv_evict_first), which keeps the matrix and the vectors that the
+// CGS kernels read next; measured on a B300, evict-first loads in the CGS kernels
+// themselves cost more than they saved.
 // ===========================================================================
 
 // Partial-sum buffers of one Arnoldi step (working type, column-major: column c of a
@@ -375,13 +388,9 @@ struct StepParts {
   W* p2;       // k_cgs_u1: j+1 columns, g2 CTAs
   W* p3;       // k_cgs_u2: 1 column, g2 CTAs
   int g1, g2;
+  // p1[j & 1] without dynamic indexing (which would copy the parameter to local memory)
+  __device__ __forceinline__ W* p1_of(int j) const { return (j & 1) ? p1[1] : p1[0]; }
 };
-
-// Column sums of per-CTA partials into shared memory: out[c] = sum_b part[c G + b].
-template <class W>
-__device__ __forceinline__ void cta_column_sums(const W* __restrict__ part, int ncol, int G, W* out) {
-  block_reduce_columns(part, ncol, G, [&](int c, W v) { out[c] = v; });
-}
 
 // CTA sum of the per-warp accumulators acc_w[c] (warp w's at acc0 + w * stride) written
 // as this CTA's partial of each column.
@@ -395,28 +404,87 @@ __device__ __forceinline__ void write_cta_partials(const W* acc0, int stride, in
   }
 }
 
-// Givens update of step js (Algorithm 1's least squares solved incrementally, FP64) with
-// the stop decision.  Called by every thread of the CTA; `sh` holds 3 (js + 2) + 2
-// doubles of shared memory.  Returns (through *done_out / *sigma_out, valid in all
-// threads after the call) whether the cycle ends and 1 / h_{js+1,js}.  If `writer`, the
-// CTA stores H[:, js], R[:, js], the rotation, |g_{js+1}|, the history and the flags.
+// ---------------------------------------------------------------------------
+// Column sums shared across a thread-block cluster.
+//
+// Every CTA of a step kernel needs the sums over the previous kernel's CTAs of a few
+// columns of partials.  Summing every column in every CTA is slow on a B300 (6-17 us for
+// 1-51 columns of ~300 partials, with all CTAs reading the same lines at once), so rank
+// r of each cluster of CL CTAs sums only the columns c with c % CL == r (one warp per
+// column, in the fixed order of warp_sum_partials), and the cluster exchanges the sums
+// through distributed shared memory.  Every CTA ends with bitwise the same values.
+//
+// The CTAs of a cluster must reach the same cluster barriers, so the skip decision is
+// made per cluster: a CTA whose own flag is clear still skips when another CTA of its
+// cluster saw the flag set (which only happens when a CTA of the same launch has just
+// ended the cycle or the solve, so the work would be discarded anyway).
+// ---------------------------------------------------------------------------
+constexpr int CL = 4;  // CTAs per cluster of the step kernels
+
 template <class W>
-__device__ void finalize_step(DevState* st, const Arrays& a, int js, const W* __restrict__ p3,
-                              int g3, const W* __restrict__ p1, int g1, bool writer, double* sh,
-                              int* done_out, double* sigma_out) {
+struct ColumnSrc {    // column c of the partials: `count` values at `ptr`
+  const W* ptr;
+  int count;
+};
+
+// col(c) -> ColumnSrc<W>.  mine and out hold ncol values (shared memory); *s_skip is this
+// CTA's skip flag (shared memory, set before the call).  Returns false when the cluster
+// skips; then out is not written.  Called by all threads of every CTA of the cluster.
+template <class W, class ColF>
+__device__ __forceinline__ bool cluster_column_sums(const ColF& col, int ncol, W* mine, W* out,
+                                                    const int* s_skip) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int s_any;
+  if (!*s_skip) {
+    for (int c = rank + CL * warp; c < ncol; c += CL * NWARP) {
+      const ColumnSrc<W> src = col(c);
+      const W v = warp_sum_partials(src.ptr, src.count);
+      if (lane == 0) mine[c] = v;
+    }
+  }
+  cl.sync();
+  if (warp == 0) {
+    int f = lane < CL ? *cl.map_shared_rank(s_skip, lane) : 0;
+    f = __any_sync(0xffffffffu, f);
+    if (lane == 0) s_any = f;
+  }
+  __syncthreads();
+  const int any = s_any;
+  if (!any)
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) out[c] = *cl.map_shared_rank(mine + c, c % CL);
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+  return !any;
+}
+
+// Shared-memory doubles that finalize_step needs (for js < LSQ_MAX).
+constexpr int GIVENS_SH = 4 * (LSQ_MAX + 2);
+
+// Givens update of step js (Algorithm 1's least squares solved incrementally, FP64) with
+// the stop decision.  Called by every thread of the CTA; `sh` holds GIVENS_SH doubles of
+// shared memory.  Returns (through *done_out / *sigma_out, valid in all threads after the
+// call) whether the cycle ends and 1 / h_{js+1,js}.  If `writer`, the CTA stores
+// H[:, js], R[:, js], the rotation, |g_{js+1}|, the history and the flags.
+// hn2 = ||w''||^2 and wn2 = ||A v_js||^2 are the column sums of the partials of
+// k_cgs_u2(js) and of the norm column of k_spmv_sell(js) (the same values in every CTA).
+//
+// The previous rotations G_0 .. G_{js-1} act on the new column h as a chain: with x_0 =
+// h_0, rotation i gives R_{i,js} = c_i x_i + s_i h_{i+1} and x_{i+1} = -s_i x_i + c_i h_{i+1},
+// an affine recurrence in x.  FP64 instructions are slow on a B300 and a serial chain of
+// 4 js of them costs about 0.2 us per rotation, so warp 0 evaluates it as a scan: each lane
+// composes the affine maps of a segment of rotations, a shuffle scan gives every lane the
+// x entering its segment, and the lanes replay their segments in parallel.
+__device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2, double wn2,
+                              bool writer, double* sh, int* done_out, double* sigma_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* col = sh;                 // js + 2
+  double* col = sh;                 // js + 2: the new column h (H[:, js] before rotation)
   double* cs = sh + (js + 2);       // js
   double* sn = cs + (js + 1);       // js
-  double* nrm = sn + (js + 1);      // [0] = ||w''||^2, [1] = ||A v_js||^2
+  double* rot = sn + (js + 1);      // js: R[0..js, js]
   const int ldh = st->m + 1;
-  if (warp == 0) {
-    const W v = warp_sum_partials(p3, g3);
-    if (lane == 0) nrm[0] = (double)v;
-  } else if (warp == 1) {
-    const W v = warp_sum_partials(p1 + (long long)(js + 1) * g1, g1);
-    if (lane == 0) nrm[1] = (double)v;
-  } else if (warp == 2) {
+  if (warp == 2) {
     double* Hc = a.H + (long long)js * ldh;
     for (int i = lane; i <= js; i += 32) {
       const double h = a.h1[i] + a.h2[i];
@@ -432,48 +500,77 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, const W* __
   __syncthreads();
   __shared__ int s_done;
   __shared__ double s_sigma;
-  if (tid == 0) {
-    const double hn = sqrt(nrm[0]), wnorm = sqrt(nrm[1]);
-    for (int i = 0; i < js; ++i) {
-      const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-      col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-      col[i] = t;
+  if (warp == 0) {
+    const unsigned full = 0xffffffffu;
+    const int seg = (js + 31) / 32;
+    const int i0 = min(lane * seg, js), i1 = min(i0 + seg, js);
+    // this lane's composite map x -> A x + B over rotations [i0, i1)
+    double A = 1.0, B = 0.0;
+    for (int i = i0; i < i1; ++i) {
+      const double ai = -sn[i], bi = cs[i] * col[i + 1];
+      B = fma(ai, B, bi);
+      A = ai * A;
     }
-    const double x = col[js];
-    double c = 1.0, s = 0.0;
-    if (hn != 0.0) {
-      const double rho = hypot(x, hn);
-      c = x / rho;
-      s = hn / rho;
-    }
-    col[js] = c * x + s * hn;
-    col[js + 1] = 0.0;
-    const double res = a.gabs[js] * fabs(s);
-    const long long iters = st->iters0 + js + 1;
-    const bool bad = !isfinite(hn) || !isfinite(res) || !isfinite(col[js]);
-    const int brk = hn <= 16.0 * st->u_work * wnorm;
-    const int done = bad || brk || res <= st->stop_rel || js + 1 >= st->m || iters >= st->max_iters;
-    s_done = done;
-    s_sigma = brk ? 0.0 : 1.0 / hn;
-    if (writer) {
-      double* Hc = a.H + (long long)js * ldh;
-      double* Rc = a.R + (long long)js * ldh;
-      Hc[js + 1] = hn;
-      for (int i = 0; i <= js + 1; ++i) Rc[i] = col[i];
-      a.cs[js] = c;
-      a.sn[js] = s;
-      a.gabs[js + 1] = res;
-      st->k = js + 1;
-      st->iters = iters;
-      if (iters <= st->hist_cap)
-        a.hist[iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
-      st->breakdown = brk;
-      if (bad) {
-        st->status = ST_NONFINITE;
-        st->stop = 1;
+    // inclusive scan: lane l holds the composite of the segments of lanes 0..l
+    for (int d = 1; d < 32; d <<= 1) {
+      const double Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+      if (lane >= d) {
+        B = fma(A, Bp, B);
+        A = A * Ap;
       }
-      if (done) st->cycle_done = 1;
-      st->sigma = s_sigma;
+    }
+    const double Ae = __shfl_up_sync(full, A, 1), Be = __shfl_up_sync(full, B, 1);
+    double x = col[0];
+    if (lane > 0) x = fma(Ae, x, Be);  // x entering this lane's segment
+    for (int i = i0; i < i1; ++i) {
+      const double h = col[i + 1];
+      rot[i] = fma(cs[i], x, sn[i] * h);
+      x = fma(-sn[i], x, cs[i] * h);
+    }
+    // x_js: the value leaving the last lane's segment (lane 31's composite covers all)
+    x = js > 0 ? fma(__shfl_sync(full, A, 31), col[0], __shfl_sync(full, B, 31)) : col[0];
+    __syncwarp();
+    if (writer) {
+      double* Rc = a.R + (long long)js * ldh;
+      for (int i = lane; i < js; i += 32) Rc[i] = rot[i];
+    }
+    if (lane == 0) {
+      const double hn = sqrt(hn2), wnorm = sqrt(wn2);
+      double c = 1.0, s = 0.0;
+      if (hn != 0.0) {
+        const double rho = hypot(x, hn);
+        c = x / rho;
+        s = hn / rho;
+      }
+      const double rjj = c * x + s * hn;
+      const double res = a.gabs[js] * fabs(s);
+      const long long iters = st->iters0 + js + 1;
+      const bool bad = !isfinite(hn) || !isfinite(res) || !isfinite(rjj);
+      const int brk = hn <= 16.0 * st->u_work * wnorm;
+      const int done = bad || brk || res <= st->stop_rel || js + 1 >= st->m || iters >= st->max_iters;
+      s_done = done;
+      s_sigma = brk ? 0.0 : 1.0 / hn;
+      if (writer) {
+        double* Hc = a.H + (long long)js * ldh;
+        double* Rc = a.R + (long long)js * ldh;
+        Hc[js + 1] = hn;
+        Rc[js] = rjj;
+        Rc[js + 1] = 0.0;
+        a.cs[js] = c;
+        a.sn[js] = s;
+        a.gabs[js + 1] = res;
+        st->k = js + 1;
+        st->iters = iters;
+        if (iters <= st->hist_cap)
+          a.hist[iters - 1] = res * st->gamma / (st->bnorm > 0.0 ? st->bnorm : 1.0);
+        st->breakdown = brk;
+        if (bad) {
+          st->status = ST_NONFINITE;
+          st->stop = 1;
+        }
+        if (done) st->cycle_done = 1;
+        st->sigma = s_sigma;
+      }
     }
   }
   __syncthreads();
@@ -497,7 +594,7 @@ struct SellSmem {
 // range of warp tiles (cta_begin).  PLAIN: src is p(A) v_j (working type, unscaled),
 // gathered as is; V[:, j] was stored by the polynomial's first kernel.
 template <int P, class SrcT, bool PLAIN>
-__global__ void __launch_bounds__(NT, 2) k_spmv_sell(
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     const int2* __restrict__ meta, const int* __restrict__ sc, const typename Tr<P>::S* __restrict__ sv,
     int nslices, int n, long long ld, double row_scale_d, const SrcT* __restrict__ src,
     double v_scale, typename Tr<P>::S* V, int j, typename Tr<P>::W* __restrict__ wout,
@@ -507,25 +604,30 @@ __global__ void __launch_bounds__(NT, 2) k_spmv_sell(
   constexpr int VEC = Tr<P>::VEC;
   constexpr int WT = SellSmem<P>::WT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
+  __shared__ double gsh[GIVENS_SH];
   const int ncol = j + 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   W* ws = reinterpret_cast<W*>(smem_raw) + (size_t)warp * (WT + ncol);
   W* acc = ws + WT;
   __shared__ int s_skip;
+  __shared__ W s_mine[2], s_nrm[2];
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
-  if (s_skip) return;
   double sigma = 1.0;
-  if constexpr (!PLAIN) {  // with a polynomial, k_poly_start applied the update
-    if (j > 0) {
-      int done;
-      finalize_step(st, arr, j - 1, parts.p3, parts.g2, parts.p1[(j - 1) & 1], parts.g1,
-                    blockIdx.x == 0, gsh, &done, &sigma);
-      if (done) return;
-    } else {
-      sigma = st->sigma;
-    }
+  if (!PLAIN && j > 0) {  // with a polynomial, k_poly_start applied the update
+    // ||w''|| of step j-1 (k_cgs_u2's partials) and ||A v_{j-1}|| (norm column of step j-1)
+    const W* pn = parts.p1_of(j - 1) + (long long)j * parts.g1;
+    const auto col = [&](int c) {
+      return c == 0 ? ColumnSrc<W>{parts.p3, parts.g2} : ColumnSrc<W>{pn, parts.g1};
+    };
+    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, &s_skip)) return;
+    int done;
+    finalize_step(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh, &done,
+                  &sigma);
+    if (done) return;
+  } else {
+    if (s_skip) return;
+    if (!PLAIN) sigma = st->sigma;
   }
   for (int c = lane; c < ncol; c += 32) acc[c] = W(0);
   __syncwarp();
@@ -539,8 +641,10 @@ __global__ void __launch_bounds__(NT, 2) k_spmv_sell(
   };
   S* Vj = V + (long long)j * ld;
   const int nwt = (n + WT - 1) / WT;
-  const int t1 = (int)cta_begin(nwt, 1, 1);
-  for (int wt = (int)cta_begin(nwt, 1) + warp; wt < t1; wt += NWARP) {
+  const int t0 = (int)cta_begin(nwt, 1), t1 = (int)cta_begin(nwt, 1, 1);
+  const bool rev = j & 1;  // traversal direction: see "Row order" above
+  for (int k = warp; k < t1 - t0; k += NWARP) {
+    const int wt = rev ? t1 - 1 - k : t0 + k;
     const int r0 = wt * WT;
     const int s0 = r0 >> 5;
     int2 mt[VEC];
@@ -585,12 +689,14 @@ __global__ void __launch_bounds__(NT, 2) k_spmv_sell(
     W nrm = W(0);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
-    dots_to_acc<S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc);
+    // columns 0..j-1 are read-only here (evict-first); column j was just stored by the warp
+    dots_to_acc<true, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j, wv, acc);
+    dots_to_acc<false, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc, j);
     nrm = warp_sum(nrm);
     if (lane == 0) acc[j + 1] += nrm;
   }
   __syncthreads();
-  write_cta_partials(reinterpret_cast<W*>(smem_raw) + WT, WT + ncol, ncol, parts.p1[j & 1]);
+  write_cta_partials(reinterpret_cast<W*>(smem_raw) + WT, WT + ncol, ncol, parts.p1_of(j));
 }
 
 // Store V[:, j] = store(v_scale * sigma * src) for all rows (the last basis vector of
@@ -606,18 +712,19 @@ __global__ void k_store_basis(const SrcT* __restrict__ src, double v_scale, int 
     Vj[i] = to_s<S>(f * src[i]);
 }
 
-// Prologue shared by the CGS kernels.  The partials hold dot products with the stored
-// (scaled) basis, so h[c] = (column sum) / v_scale is v_c . w; the update multiplies the
-// stored basis, so its coefficient is coef[c] = h[c] / v_scale.  CTA 0 stores h in FP64.
+// Prologue shared by the CGS kernels.  coef[c] holds on entry the column sum of the
+// partials, i.e. the dot product with the stored (scaled) basis, so h[c] = coef[c] /
+// v_scale is v_c . w; the update multiplies the stored basis, so its coefficient becomes
+// h[c] / v_scale.  CTA 0 stores h in FP64.
 template <class W>
-__device__ __forceinline__ void load_coefs(const W* __restrict__ part, int nc, int G, double v_scale,
-                                           W* coef, double* __restrict__ h) {
+__device__ __forceinline__ void coefs_from_sums(W* coef, int nc, double v_scale,
+                                                double* __restrict__ h) {
   const bool writer = blockIdx.x == 0;
-  block_reduce_columns(part, nc, G, [&](int c, W v) {
-    const double hc = (double)v / v_scale;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const double hc = (double)coef[c] / v_scale;
     coef[c] = (W)(hc / v_scale);
     if (writer) h[c] = hc;
-  });
+  }
   __syncthreads();
 }
 
@@ -625,7 +732,7 @@ __device__ __forceinline__ void load_coefs(const W* __restrict__ part, int nc, i
 // Step kernel 2: h1 (prologue), w' = w - V_j h1, partials of V_j^T w'.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(NT, 2) k_cgs_u1(const typename Tr<P>::S* __restrict__ V, long long ld,
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_cgs_u1(const typename Tr<P>::S* __restrict__ V, long long ld,
                                                int j, double v_scale,
                                                const typename Tr<P>::W* __restrict__ win,
                                                typename Tr<P>::W* __restrict__ wout,
@@ -639,21 +746,27 @@ __global__ void __launch_bounds__(NT, 2) k_cgs_u1(const typename Tr<P>::S* __res
   W* coef = reinterpret_cast<W*>(smem_raw);
   W* acc = coef + nc;
   __shared__ int s_skip;
+  __shared__ W s_mine[LSQ_MAX + 2];
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
-  if (s_skip) return;
+  const W* pj = parts.p1_of(j);
+  const int gp = parts.g1;
+  const auto col = [&](int c) { return ColumnSrc<W>{pj + (long long)c * gp, gp}; };
+  if (!cluster_column_sums<W>(col, nc, s_mine, coef, &s_skip)) return;
   for (int i = tid; i < NWARP * nc; i += NT) acc[i] = W(0);
-  load_coefs(parts.p1[j & 1], nc, parts.g1, v_scale, coef, h1);
+  coefs_from_sums(coef, nc, v_scale, h1);
   const long long ngroups = ld / VEC;
   const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
-  for (long long g = g0 + tid; g < g1; g += NT) {
+  const bool rev = !(j & 1);  // traversal direction: see "Row order" above
+  for (long long i = tid; i < g1 - g0; i += NT) {
+    const long long g = rev ? g1 - 1 - i : g0 + i;
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
-    update_all<S, W, VEC>(V, ld, base, nc, coef, wv);
+    update_all<false, S, W, VEC>(V, ld, base, nc, coef, wv);
     stv(wout + base, wv);
-    dots_to_acc<S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
+    dots_to_acc<false, S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
   }
   __syncthreads();
   write_cta_partials(acc, nc, nc, parts.p2);
@@ -663,7 +776,7 @@ __global__ void __launch_bounds__(NT, 2) k_cgs_u1(const typename Tr<P>::S* __res
 // Step kernel 3: h2 (prologue), w'' = w' - V_j h2, partials of ||w''||^2.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(NT, 2) k_cgs_u2(const typename Tr<P>::S* __restrict__ V, long long ld,
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_cgs_u2(const typename Tr<P>::S* __restrict__ V, long long ld,
                                                int j, double v_scale,
                                                const typename Tr<P>::W* __restrict__ win,
                                                typename Tr<P>::W* __restrict__ wout,
@@ -677,19 +790,25 @@ __global__ void __launch_bounds__(NT, 2) k_cgs_u2(const typename Tr<P>::S* __res
   W* coef = reinterpret_cast<W*>(smem_raw);
   __shared__ W accw[NWARP];
   __shared__ int s_skip;
+  __shared__ W s_mine[LSQ_MAX + 2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
-  if (s_skip) return;
-  load_coefs(parts.p2, nc, parts.g2, v_scale, coef, h2);
+  const W* pj = parts.p2;
+  const int gp = parts.g2;
+  const auto col = [&](int c) { return ColumnSrc<W>{pj + (long long)c * gp, gp}; };
+  if (!cluster_column_sums<W>(col, nc, s_mine, coef, &s_skip)) return;
+  coefs_from_sums(coef, nc, v_scale, h2);
   W nrm = W(0);
   const long long ngroups = ld / VEC;
   const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
-  for (long long g = g0 + tid; g < g1; g += NT) {
+  const bool rev = j & 1;  // traversal direction: see "Row order" above
+  for (long long i = tid; i < g1 - g0; i += NT) {
+    const long long g = rev ? g1 - 1 - i : g0 + i;
     const long long base = g * VEC;
     W wv[VEC];
     ldv(win + base, wv);
-    update_all<S, W, VEC>(V, ld, base, nc, coef, wv);
+    update_all<false, S, W, VEC>(V, ld, base, nc, coef, wv);
     stv(wout + base, wv);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
@@ -709,7 +828,7 @@ __global__ void __launch_bounds__(NT, 2) k_cgs_u2(const typename Tr<P>::S* __res
 template <int P>
 __global__ void __launch_bounds__(NT) k_finalize(StepParts<typename Tr<P>::W> parts, DevState* st,
                                                  Arrays arr) {
-  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
+  __shared__ double gsh[GIVENS_SH];
   __shared__ int s_go, s_js;
   if (threadIdx.x == 0) {
     s_js = st->last_step;
@@ -717,10 +836,19 @@ __global__ void __launch_bounds__(NT) k_finalize(StepParts<typename Tr<P>::W> pa
   }
   __syncthreads();
   if (!s_go) return;
+  using W = typename Tr<P>::W;
+  __shared__ double s_n[2];
+  const int warp = threadIdx.x >> 5;
+  if (warp < 2) {
+    const W v = warp == 0 ? warp_sum_partials(parts.p3, parts.g2)
+                          : warp_sum_partials(parts.p1_of(s_js) + (long long)(s_js + 1) * parts.g1,
+                                              parts.g1);
+    if ((threadIdx.x & 31) == 0) s_n[warp] = (double)v;
+  }
+  __syncthreads();
   int done;
   double sigma;
-  finalize_step(st, arr, s_js, parts.p3, parts.g2, parts.p1[s_js & 1], parts.g1, true, gsh, &done,
-                &sigma);
+  finalize_step(st, arr, s_js, s_n[0], s_n[1], true, gsh, &done, &sigma);
 }
 
 // ---------------------------------------------------------------------------

@@ -23,28 +23,37 @@ __device__ __forceinline__ int poly_skip(const DevState* st, int in_cycle) {
 }
 
 // First kernel of p(A) v_j inside an Arnoldi step.  For j > 0 it first applies the
-// Givens update of step j-1 (every CTA computes it, CTA 0 stores it: see k_spmv_sell),
+// Givens update of step j-1 (every CTA computes it from the cluster's column sums, CTA 0
+// stores it: see k_spmv_sell),
 // which gives 1 / h_{j,j-1}; then V[:, j] = store(v_scale * sigma * src) (the
 // normalisation of the previous step) and prod = v_j in the working type.
 template <int P, class SrcT>
-__global__ void __launch_bounds__(NT) k_poly_start(const SrcT* __restrict__ src, double v_scale,
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(const SrcT* __restrict__ src, double v_scale,
                                                    int n, typename Tr<P>::S* V, long long ld,
                                                    int j, typename Tr<P>::W* __restrict__ prod,
                                                    StepParts<typename Tr<P>::W> parts,
                                                    DevState* st, Arrays arr) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  __shared__ double gsh[3 * (LSQ_MAX + 2) + 2];
+  __shared__ double gsh[GIVENS_SH];
   __shared__ int s_skip;
+  __shared__ W s_mine[2], s_nrm[2];
   if (threadIdx.x == 0) s_skip = poly_skip(st, 1);
   __syncthreads();
-  if (s_skip) return;
-  double sigma = st->sigma;
+  double sigma;
   if (j > 0) {
+    const W* pn = parts.p1_of(j - 1) + (long long)j * parts.g1;
+    const auto col = [&](int c) {
+      return c == 0 ? ColumnSrc<W>{parts.p3, parts.g2} : ColumnSrc<W>{pn, parts.g1};
+    };
+    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, &s_skip)) return;
     int done;
-    finalize_step(st, arr, j - 1, parts.p3, parts.g2, parts.p1[(j - 1) & 1], parts.g1,
-                  blockIdx.x == 0, gsh, &done, &sigma);
+    finalize_step(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh, &done,
+                  &sigma);
     if (done) return;
+  } else {
+    if (s_skip) return;
+    sigma = st->sigma;
   }
   const SrcT f = (SrcT)(v_scale * sigma);
   const W inv = (W)(1.0 / v_scale);

@@ -18,6 +18,7 @@
 
 #include "gmres_ir.h"
 #include "kernels.cuh"
+#include "cgs_tma.cuh"
 #include "poly_kernels.cuh"
 #include "poly_host.h"
 
@@ -208,12 +209,26 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
       k_spmv_sell<P, W, false><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, w3,
           pl.v_scale, V, j, w1, sp, pl.st, pl.arr);
-  } else if (which == 1) {
-    k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1) * (1 + NWARP), s>>>(
-        V, pl.ld, j, pl.v_scale, w1, w2, sp, pl.st, pl.arr.h1);
   } else {
-    k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)(j + 1), s>>>(V, pl.ld, j, pl.v_scale, w2,
-                                                                     w3, sp, pl.st, pl.arr.h2);
+    // Both forms run on grid_vec CTAs, so the partial-sum layout does not depend on the form.
+    const int nc = j + 1;
+    const int ns = pl.p.cgs_kernel == GMRES_CGS_TMA ? TmaLayout<P>::stages(nc) : 0;
+    const size_t tb = TmaLayout<P>::bytes(nc, ns);
+    if (which == 1) {
+      if (ns && nc <= TMA_U1_MAX_COLS)
+        k_cgs_u1_tma<P><<<pl.grid_vec, TMA_THREADS, tb, s>>>(V, pl.ld, j, pl.v_scale, w1, w2, sp,
+                                                             pl.st, pl.arr.h1, ns);
+      else
+        k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)nc * (1 + NWARP), s>>>(
+            V, pl.ld, j, pl.v_scale, w1, w2, sp, pl.st, pl.arr.h1);
+    } else {
+      if (ns)
+        k_cgs_u2_tma<P><<<pl.grid_vec, TMA_THREADS, tb, s>>>(V, pl.ld, j, pl.v_scale, w2, w3, sp,
+                                                             pl.st, pl.arr.h2, ns);
+      else
+        k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)nc, s>>>(V, pl.ld, j, pl.v_scale, w2,
+                                                                    w3, sp, pl.st, pl.arr.h2);
+    }
   }
 }
 
@@ -265,6 +280,22 @@ static void launch_cycle(Plan& pl, cudaStream_t s) {
   launch_cycle_tail<P>(pl, s);
 }
 
+// Grid of a cluster kernel: `want` CTAs rounded up to a multiple of CL, capped at the
+// clusters that fit on the GPU at once.
+template <class K>
+static int cluster_grid(K* kernel, size_t smem, long long want, int* grid) {
+  const long long want_cl = std::max(1LL, (want + CL - 1) / CL);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(want_cl * CL));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  int ncl = 0;
+  CK(cudaOccupancyMaxActiveClusters(&ncl, kernel, &cfg));
+  if (ncl < 1) return note_cuda(cudaErrorInvalidConfiguration, __LINE__);
+  *grid = (int)(CL * std::min<long long>(want_cl, ncl));
+  return GMRES_OK;
+}
+
 template <int P>
 static int configure(Plan& pl) {
   using W = typename Tr<P>::W;
@@ -282,20 +313,23 @@ static int configure(Plan& pl) {
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
   CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(W) * (size_t)(LSQ_MAX + 1) * (1 + NWARP))));
+  CK(cudaFuncSetAttribute(k_cgs_u1_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)TMA_SMEM_BUDGET));
+  CK(cudaFuncSetAttribute(k_cgs_u2_tma<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)TMA_SMEM_BUDGET));
   CK(cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(double) * LSQ_PACKED_MAX * (LSQ_PACKED_MAX + 1) / 2)));
   pl.grid_elem = pl.sms * 8;
-  int occ = 1;
   // At most two CTAs per SM, each with an equal contiguous share of the rows (the kernels
-  // split the work with cta_begin): no second wave, and the cross-CTA reductions sum about
-  // 2 x #SMs partials per column.
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_sell<P, W, false>, NT, sm_max));
+  // split the work with cta_begin): no second wave.  The step kernels run in clusters of
+  // CL CTAs, so their grids are multiples of CL and hold no more clusters than the GPU
+  // keeps resident at once (GPCs whose SM count is not a multiple of the cluster's leave a
+  // few SMs out).
   const long long nwt = (pl.n + SellSmem<P>::WT - 1) / SellSmem<P>::WT;
-  pl.grid_spmv = (int)std::max(1LL, std::min(nwt, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_u1<P>, NT, sm_u1));
+  int e = cluster_grid(k_spmv_sell<P, W, false>, sm_max, std::min(nwt, 2LL * pl.sms), &pl.grid_spmv);
+  if (e) return e;
   const long long nchunks = pl.ld / VEC / 32;  // 32-group chunks (one warp's worth)
-  pl.grid_vec = (int)std::max(1LL, std::min(nchunks, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
-  return GMRES_OK;
+  return cluster_grid(k_cgs_u1<P>, sm_u1, std::min(nchunks, 2LL * pl.sms), &pl.grid_vec);
 }
 
 static int configure_residual(Plan& pl) {
@@ -362,6 +396,7 @@ static int validate_params(const gmres_params* p) {
   if (p->inner_prec < 0 || p->inner_prec > 3) return GMRES_ERR_INVALID;
   if (p->poly_degree < 0) return GMRES_ERR_INVALID;
   if (p->poly_degree > GMRES_MAX_POLY_DEGREE) return GMRES_ERR_TOO_LARGE;
+  if (p->cgs_kernel != GMRES_CGS_REGISTER && p->cgs_kernel != GMRES_CGS_TMA) return GMRES_ERR_INVALID;
   return GMRES_OK;
 }
 
@@ -670,6 +705,7 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
   for (int c = 0; c < steps; ++c)
     for (int i = 0; i <= steps; ++i)
       H_out[i + (size_t)c * (steps + 1)] = (c < k && i <= c + 1) ? Hfull[i + (size_t)c * (pl.m + 1)] : 0.0;
+  if (pl.h_st->status == ST_TIMEOUT) return GMRES_ERR_DEVICE_TIMEOUT;
   return pl.h_st->status == ST_NONFINITE ? GMRES_NONFINITE : GMRES_OK;
 }
 
@@ -757,6 +793,7 @@ const char* gmres_status_string(int status) {
     case GMRES_ERR_OOM: return "device allocation failed";
     case GMRES_ERR_CUDA: return "CUDA runtime error";
     case GMRES_ERR_TOO_LARGE: return "size exceeds a documented maximum";
+    case GMRES_ERR_DEVICE_TIMEOUT: return "a device-side bounded wait expired";
   }
   return "unknown status";
 }

@@ -5,6 +5,7 @@ FP64 residual of x0 = 0 and one cycle of m Arnoldi steps launched one kernel at 
 printing the per-launch device times measured with CUDA events.
 
     python -m paper_2109_01232_b300.profile_case [--side 100] [--prec fp32] [--m 50]
+        [--cgs-kernel register|tma]
 """
 from __future__ import annotations
 
@@ -28,11 +29,13 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=list(g.PREC))
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--peclet", type=float, default=10.0)
+    ap.add_argument("--cgs-kernel", default="register", choices=list(g.CGS_KERNEL))
     args = ap.parse_args()
     p, b = gen.config_3d(args.peclet, side=args.side)
     A = g.DeviceCSR.from_problem(p)
     kind = "gmres" if args.prec == "fp64" else "ir"
-    plan = g.Plan(A, kind, restart_m=args.m, inner_prec=args.prec if kind == "ir" else "fp32")
+    plan = g.Plan(A, kind, restart_m=args.m, inner_prec=args.prec if kind == "ir" else "fp32",
+                  cgs_kernel=args.cgs_kernel)
     bt = torch.tensor(b, device="cuda")
     x0 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     ms = plan.profile_cycle(bt, x0)

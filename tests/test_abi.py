@@ -48,17 +48,17 @@ def test_struct_layout_matches_c(tmp_path, lib):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "gmres_ir.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(gmres_csr),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(gmres_csr),"
         " sizeof(gmres_params), sizeof(gmres_stats), offsetof(gmres_params, seed),"
         " offsetof(gmres_stats, history), offsetof(gmres_params, record_history),"
-        " offsetof(gmres_stats, rel_resid)); return 0;}\n")
+        " offsetof(gmres_stats, rel_resid), offsetof(gmres_params, cgs_kernel)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                        check=True).stdout.split()))
     want = [ctypes.sizeof(g.csr_t), ctypes.sizeof(g.params_t), ctypes.sizeof(g.stats_t),
             g.params_t.seed.offset, g.stats_t.history.offset, g.params_t.record_history.offset,
-            g.stats_t.rel_resid.offset]
+            g.stats_t.rel_resid.offset, g.params_t.cgs_kernel.offset]
     assert got == want
 
 
@@ -66,8 +66,10 @@ def test_default_params_and_status_strings(lib):
     import paper_2109_01232_b300 as g
     p = g.default_params()
     assert (p.restart_m, p.rtol, p.inner_prec, p.poly_degree) == (50, 1e-10, 1, 0)
-    for code in range(8):
+    assert p.cgs_kernel == g.CGS_KERNEL["register"]
+    for code in range(9):
         assert lib.gmres_status_string(code)
+    assert b"wait" in lib.gmres_status_string(g.ERR_DEVICE_TIMEOUT)
     assert g.MAX_RESTART == 512
 
 
@@ -84,5 +86,7 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.gmres_ir_solve(ctypes.byref(c), 1, 1, ctypes.byref(big), ctypes.byref(st), None) == g.ERR_TOO_LARGE
     neg = g.default_params(rtol=-1.0)
     assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(neg), ctypes.byref(st), None) == g.ERR_INVALID
+    form = g.default_params(cgs_kernel=7)
+    assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(form), ctypes.byref(st), None) == g.ERR_INVALID
     empty = g.csr_t(0, 0, None, None, None)
     assert lib.gmres_ir_solve(ctypes.byref(empty), 1, 1, ctypes.byref(p), ctypes.byref(st), None) == g.OK

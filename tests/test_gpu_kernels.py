@@ -124,6 +124,34 @@ def test_arnoldi_low_precision(g, torch, prec, orth_tol, rel_tol, h_tol):
     plan.close()
 
 
+# steps chosen so that the TMA-fed CGS kernels run for the first steps and the register
+# kernels for the last ones (the basis block of a step stops fitting two shared-memory
+# stages at 26 columns in FP64 and 53 in FP32; u1 keeps 64 column accumulators)
+@pytest.mark.parametrize("prec,steps,tol", [
+    ("fp64", 30, 1e-12), ("fp32", 56, 2e-5), ("fp16", 68, 2e-3), ("bf16", 68, 2e-2)])
+def test_arnoldi_cgs_kernel_forms_agree(g, torch, prec, steps, tol):
+    """The TMA-fed and register-fed CGS2 kernels compute the same step (only the order of
+    the row sums inside a CTA differs), so the Hessenberg matrices agree to rounding."""
+    p = PROBLEMS["3d"]()  # n = 4913: 20 row blocks of 256 and a ragged tail
+    v0 = torch.tensor(oracle.splitmix64_uniform(8, p.n), device="cuda")
+    A = g.DeviceCSR.from_problem(p)
+    kind = "gmres" if prec == "fp64" else "ir"
+    ip = prec if prec != "fp64" else "fp32"
+    Hs = []
+    for form in ("tma", "register"):
+        plan = g.Plan(A, kind, restart_m=steps, inner_prec=ip, cgs_kernel=form)
+        V, H, k = plan.arnoldi(v0, steps)
+        assert k == steps
+        Hs.append(H)
+        plan.close()
+    nA = np.abs(oracle.dense(p)).sum(axis=1).max()
+    # the first steps agree to the working precision; later ones drift apart at most as
+    # fast as the Arnoldi process amplifies rounding in the low-precision basis
+    assert np.abs(Hs[0][:9, :8] - Hs[1][:9, :8]).max() <= tol * nA
+    for H in Hs:
+        assert np.isfinite(H).all()
+
+
 def test_poly_roots_match_oracle(g, torch):
     p = gen.conv_diff_2d(40, 60.0, (1.0, 0.3))
     A = g.DeviceCSR.from_problem(p)
