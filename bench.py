@@ -18,6 +18,8 @@ solve does not shard on this single-GPU design); the reported time is the max ov
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -144,6 +146,39 @@ def roofline(ms: np.ndarray, n: int, nnz: int, prec: int):
     return dom, out
 
 
+# ------------------------------------------------------ measured traffic ----
+PROFILE_OF = {"spmv": "k_spmv_sell_3d100_fp32.md", "u1": "k_cgs_u1_3d100_fp32.md",
+              "u2": "k_cgs_u2_3d100_fp32.md"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2109_01232_b300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, alg_bytes_avg: float):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary (one captured launch,
+    scaled to the cycle's average launch by the algorithmic bytes), or None when there is no
+    summary or the kernel sources changed after the capture."""
+    name = PROFILE_OF.get(kernel)
+    path = os.path.join(ROOT, "profiles", name) if name else None
+    if not path or not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            k, sep, v = line.partition(":")
+            if sep and k.strip() in ("traffic_bytes_per_launch", "alg_bytes_per_launch",
+                                     "source_sha256_16"):
+                fields[k.strip()] = v.strip()
+    if fields.get("source_sha256_16") != kernel_source_hash():
+        return None
+    return float(fields["traffic_bytes_per_launch"]) * alg_bytes_avg / float(fields["alg_bytes_per_launch"])
+
+
 # --------------------------------------------------------------- our arm ----
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -265,7 +300,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "kernel": dom,
                          "achieved": kd["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": kd["achieved_gbs"] / peak, "peak_source": peak_kind,
-                         "traffic": None,
+                         "traffic": measured_traffic(dom, kd["bytes_per_launch"]),
                          "bytes_per_launch": kd["bytes_per_launch"],
                          "avg_launch_ms": kd["ms_total"] / kd["launches"]},
             "kernels": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv)
