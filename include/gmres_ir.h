@@ -227,6 +227,67 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
 #define GMRES_NOALLOC_MAX_N (1 << 20)
 int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, double* y, void* stream);
 
+/* ---- Batched GMRES-IR: many independent small systems -------------------
+ * Each system A_i x_i = b_i is solved by GMRES-IR (Algorithm 2: FP64 residual and
+ * update, inner GMRES(m) cycle of Algorithm 1 with CGS2 in p->inner_prec) exactly as
+ * gmres_ir_solve would, but all systems run in ONE persistent kernel: every thread-block
+ * cluster takes the next unsolved system (largest first, through a device counter) and
+ * carries out its whole solve, its CTAs splitting the rows and combining their sums
+ * through distributed shared memory, so no system waits for another and no cluster waits
+ * for another cluster.  Meant for systems of up to a few 10^5 rows (the per-cluster
+ * workspace is (m+1) columns of the largest system); restart_m <= GMRES_BATCH_MAX_M.
+ *
+ * The systems are one concatenated CSR:
+ *   row_off, nnz_off: HOST, nsys+1 int64 each, non-decreasing, row_off[0] = nnz_off[0]
+ *                     = 0: system i has rows [row_off[i], row_off[i+1]) of the
+ *                     concatenated vectors and nonzeros [nnz_off[i], nnz_off[i+1]).
+ *   row_ptr: DEVICE, row_off[nsys] + nsys int32: system i's n_i + 1 LOCAL row pointers
+ *            (starting at 0) begin at row_ptr[row_off[i] + i].
+ *   col_idx: DEVICE, LOCAL column indices (0 <= c < n_i); vals: DEVICE FP64.
+ * The caller owns these arrays; a plan reads them until it is destroyed. */
+#define GMRES_BATCH_MAX_M 32
+typedef struct {
+  int32_t nsys;
+  const int64_t* row_off;
+  const int64_t* nnz_off;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* vals;
+} gmres_csr_batch;
+
+/* Per-system results (HOST arrays of nsys entries each, any may be NULL). */
+typedef struct {
+  int32_t* status;     /* gmres_status of each system */
+  int64_t* iters;      /* inner iterations */
+  int32_t* outer;      /* refinement steps */
+  double* rel_resid;   /* final explicit FP64 ||b_i - A_i x_i|| / ||b_i|| */
+  double t_solve_ms;   /* device time of the whole batch (CUDA events) */
+} gmres_batch_stats;
+
+typedef struct gmres_batch_plan_s* gmres_batch_plan;
+
+/* Creates the workspace (FP32 copy of the values, per-cluster basis and vectors), chooses
+ * the CTA size (256 or 512 threads) and the cluster size (1, 2, 4 or 8 CTAs per system) --
+ * if autotune is nonzero by timing each pair on a sample of the systems (every 8th by
+ * size, b = ones), else 256 threads in clusters of 4 -- and captures the launch as a CUDA
+ * graph.  p: restart_m (<= GMRES_BATCH_MAX_M), rtol, inner_rtol, max_iters (per system),
+ * inner_prec (GMRES_FP32, or GMRES_FP64 for plain FP64 GMRES(m) per system).
+ * Errors: INVALID (bad sizes/offsets/structure/params), TOO_LARGE (m), OOM, CUDA. */
+int gmres_batch_plan_create(gmres_batch_plan* plan, const gmres_csr_batch* A,
+                            const gmres_params* p, int32_t autotune, void* stream);
+/* b: DEVICE, row_off[nsys] doubles; x: DEVICE, the same, initial guesses on entry,
+ * solutions on exit.  Returns OK when every system converged, else the first non-OK
+ * status in system order (per-system codes in stats->status). */
+int gmres_batch_plan_solve(gmres_batch_plan plan, const double* b, double* x,
+                           gmres_batch_stats* stats, void* stream);
+/* out[0..6] = threads per CTA, CTAs, candidates timed by the autotuner, largest system's
+ * rows, basis leading dimension, inner precision, CTAs per cluster. */
+int gmres_batch_plan_info(gmres_batch_plan plan, int64_t* out);
+int gmres_batch_plan_destroy(gmres_batch_plan plan);
+/* One-shot: plan (no autotuning), solve, destroy. */
+int gmres_ir_solve_batched(const gmres_csr_batch* A, const double* b, double* x,
+                           const gmres_params* p, gmres_batch_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

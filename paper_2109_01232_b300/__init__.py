@@ -23,6 +23,7 @@ STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: "ERR_I
           5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TOO_LARGE", 8: "ERR_DEVICE_TIMEOUT"}
 (OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TOO_LARGE,
  ERR_DEVICE_TIMEOUT) = range(9)
+STATUS_SOLVER = (NOT_CONVERGED, BREAKDOWN, NONFINITE)  # outcomes of a solve, not errors
 MAX_RESTART = 512
 MAX_POLY_DEGREE = 96
 
@@ -54,6 +55,16 @@ class stats_t(ctypes.Structure):
                 ("history_cap", ctypes.c_int64)]
 
 
+class csr_batch_t(ctypes.Structure):
+    _fields_ = [("nsys", ctypes.c_int32), ("row_off", ctypes.c_void_p), ("nnz_off", ctypes.c_void_p),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+class batch_stats_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("outer", ctypes.c_void_p),
+                ("rel_resid", ctypes.c_void_p), ("t_solve_ms", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -83,6 +94,14 @@ _SIGNATURES = {
     "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
     "gmres_spmv_fp64_noalloc": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, _P]),
+    "gmres_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(csr_batch_t),
+                                               ctypes.POINTER(params_t), _I32, _P]),
+    "gmres_batch_plan_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(batch_stats_t), _P]),
+    "gmres_batch_plan_info": (ctypes.c_int, [_P, _P]),
+    "gmres_batch_plan_destroy": (ctypes.c_int, [_P]),
+    "gmres_ir_solve_batched": (ctypes.c_int, [ctypes.POINTER(csr_batch_t), _P, _P,
+                                              ctypes.POINTER(params_t),
+                                              ctypes.POINTER(batch_stats_t), _P]),
 }
 NOALLOC_MAX_N = 1 << 20
 
@@ -363,3 +382,102 @@ def spmv_fp64_noalloc(A: DeviceCSR, v, y, stream=None) -> None:
     c = A.c()
     _check(lib().gmres_spmv_fp64_noalloc(ctypes.byref(c), _ptr(v), _ptr(y), _stream(stream)),
            "spmv_fp64_noalloc")
+
+
+# ------------------------------------------------------------------ batched ----
+BATCH_MAX_M = 32
+
+
+class DeviceBatch:
+    """Many independent CSR systems concatenated for the batched solver: the local row
+    pointers of system i start at row_ptr[row_off[i] + i], its column indices are local."""
+
+    def __init__(self, problems):
+        import numpy as np
+        torch = _torch()
+        ns = [int(p.n) for p in problems]
+        zs = [int(len(p.vals)) for p in problems]
+        self.nsys = len(problems)
+        self.row_off = np.zeros(self.nsys + 1, dtype=np.int64)
+        self.nnz_off = np.zeros(self.nsys + 1, dtype=np.int64)
+        np.cumsum(ns, out=self.row_off[1:])
+        np.cumsum(zs, out=self.nnz_off[1:])
+        cat = lambda xs, dt: np.concatenate([np.asarray(x, dtype=dt) for x in xs]) if xs else np.zeros(0, dt)
+        self.row_ptr = torch.as_tensor(cat([p.row_ptr for p in problems], np.int32), device="cuda")
+        self.col_idx = torch.as_tensor(cat([p.col_idx for p in problems], np.int32), device="cuda")
+        self.vals = torch.as_tensor(cat([p.vals for p in problems], np.float64), device="cuda")
+        self.rows = int(self.row_off[-1])
+
+    def c(self) -> csr_batch_t:
+        return csr_batch_t(self.nsys, self.row_off.ctypes.data, self.nnz_off.ctypes.data,
+                           _ptr(self.row_ptr), _ptr(self.col_idx), _ptr(self.vals))
+
+    def split(self, v):
+        """Per-system views of a concatenated vector."""
+        return [v[int(self.row_off[i]):int(self.row_off[i + 1])] for i in range(self.nsys)]
+
+
+class BatchResult:
+    def __init__(self, code, status, iters, outer, relres, ms):
+        self.code, self.status, self.iters, self.outer = code, status, iters, outer
+        self.rel_resid, self.t_solve_ms = relres, ms
+
+
+class BatchPlan:
+    """Batched GMRES-IR plan: one persistent, graph-captured kernel for all systems."""
+
+    def __init__(self, batch: DeviceBatch, autotune: bool = True, stream=None, **kw):
+        self.batch = batch
+        kw.setdefault("restart_m", 30)  # the batched kernel keeps at most BATCH_MAX_M columns
+        self.params = default_params(**kw)
+        h = ctypes.c_void_p()
+        c = batch.c()
+        _check(lib().gmres_batch_plan_create(ctypes.byref(h), ctypes.byref(c),
+                                             ctypes.byref(self.params), int(bool(autotune)),
+                                             _stream(stream)), "batch_plan_create")
+        self.handle = h
+
+    def info(self) -> dict:
+        import numpy as np
+        out = np.zeros(7, dtype=np.int64)
+        _check(lib().gmres_batch_plan_info(self.handle, out.ctypes.data), "batch_plan_info")
+        keys = ("threads", "ctas", "candidates_timed", "max_rows", "ld", "prec", "cluster")
+        return dict(zip(keys, map(int, out)))
+
+    def solve(self, b, x, stream=None, allowed=(OK,)) -> BatchResult:
+        import numpy as np
+        n = self.batch.nsys
+        st = np.zeros(n, np.int32); it = np.zeros(n, np.int64)
+        ou = np.zeros(n, np.int32); rr = np.zeros(n, np.float64)
+        s = batch_stats_t(st.ctypes.data, it.ctypes.data, ou.ctypes.data, rr.ctypes.data, 0.0)
+        code = lib().gmres_batch_plan_solve(self.handle, _ptr(b), _ptr(x), ctypes.byref(s),
+                                            _stream(stream))
+        _check(code, "batch_plan_solve", allowed=tuple(allowed) + STATUS_SOLVER)
+        return BatchResult(code, st, it, ou, rr, s.t_solve_ms)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().gmres_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ir_solve_batched(batch: DeviceBatch, b, x, stream=None, **kw) -> BatchResult:
+    """One-shot batched GMRES-IR (plan without autotuning, solve, destroy)."""
+    import numpy as np
+    kw.setdefault("restart_m", 30)
+    params = default_params(**kw)
+    n = batch.nsys
+    st = np.zeros(n, np.int32); it = np.zeros(n, np.int64)
+    ou = np.zeros(n, np.int32); rr = np.zeros(n, np.float64)
+    s = batch_stats_t(st.ctypes.data, it.ctypes.data, ou.ctypes.data, rr.ctypes.data, 0.0)
+    c = batch.c()
+    code = lib().gmres_ir_solve_batched(ctypes.byref(c), _ptr(b), _ptr(x), ctypes.byref(params),
+                                        ctypes.byref(s), _stream(stream))
+    _check(code, "ir_solve_batched", allowed=(OK,) + STATUS_SOLVER)
+    return BatchResult(code, st, it, ou, rr, s.t_solve_ms)

@@ -1,0 +1,909 @@
+// batched.cuh -- GMRES-IR for many independent small systems in one persistent kernel.
+//
+// Included at the end of solver.cu (it uses the status helpers and kernels defined there).
+//
+// Each thread-block cluster of CLB CTAs (CLB = 1, 2, 4 or 8, chosen with the CTA size by the
+// plan's autotuner) takes the next unsolved system from a device counter (systems ordered
+// largest first, so the long solves start early) and runs the whole solve of it:
+// Algorithm 2's FP64 residual and update around the inner GMRES(m) cycle of Algorithm 1
+// with CGS2.  The cluster splits the system's rows into CLB contiguous ranges of VEC-row
+// groups (VEC = 4 for FP32, one 16-byte load per basis column); a thread owns groups
+// g0 + tid, g0 + tid + NTB, ... of its CTA's range, so the passes over a row read only data
+// the same thread wrote (its rows of V, w, t), and the SpMV gathers its neighbours' entries
+// of the source vector after a cluster barrier.  Reductions sum within the CTA, then
+// over the cluster's CTAs through distributed shared memory (fixed rank order), so every CTA
+// of the cluster holds bitwise the same sums and takes the same decisions; no cluster ever
+// waits for another.  Per step (j + 1 basis columns):
+//   A  v_j = store(sigma src) for own rows; w = A v_j (the gathered source is rounded the
+//      same way); sums of v_c . w (c <= j) and ||w||^2
+//   B  w' = w - V h1 and sums of v_c . w' (the second read of the row's basis values hits
+//      L1: the same thread loaded them just before)
+//   C  w'' = w' - V h2 into t (the next step's source) and ||w''||^2
+//   Givens update of the new column (warp 0, FP64 scan), stop decision
+// and at the end of a cycle: R y = g (warp 0, FP64), x += gamma V y (FP64), r = b - A x.
+// Arithmetic, rounding points and stopping rules are those of the single-system solver.
+#pragma once
+
+namespace gm {
+
+constexpr int BMAX = GMRES_BATCH_MAX_M;
+
+struct BatchSys {
+  long long row0, nnz0;  // first row / nonzero of the system in the concatenated arrays
+  int n, index;          // rows; position in the caller's order (for row_ptr and results)
+};
+
+struct BatchIO {
+  const double* b;
+  double* x;
+};
+
+template <class S, class W>
+struct BatchArgs {
+  const BatchSys* sys;     // in solve order (largest first)
+  int nsys;
+  int* counter;
+  const int* rp;           // concatenated local row pointers
+  const int* ci;
+  const double* av64;
+  const S* av;             // values in the storage precision
+  const BatchIO* io;
+  S* Vws;                  // per CTA: (m + 1) columns of ld values
+  W* wws;                  // per CTA: ld values (w, w')
+  W* tws;                  // per CTA: ld values (w'', the next source)
+  double* rws;             // per CTA: ld values (FP64 residual)
+  long long ld;
+  int m;
+  long long max_iters;
+  double rtol, inner_rtol, u_work;
+  int* status;
+  long long* iters;
+  int* outer;
+  double* relres;
+};
+
+// Sum over the cluster of acc[c] for c < cnt and of acc[BMAX]; results in out[c],
+// out[BMAX] of every CTA.  Warp sums, then the CTA's warps in order into part[ph], then (CLB
+// > 1) the cluster's CTAs in rank order through distributed shared memory.  part is double-
+// buffered by the caller's phase parity ph: a CTA rewrites part[ph] only after the next
+// reduction's cluster barrier, which every CTA reaches after its reads of this one.
+template <class W, int NW, int CLB>
+__device__ __forceinline__ void batch_reduce(const W (&acc)[BMAX + 1], int cnt, W (*red)[BMAX + 1],
+                                             W (*part)[BMAX + 1], int ph, W* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c <= BMAX; ++c) {
+    if (c < cnt || c == BMAX) {
+      const W v = warp_sum(acc[c]);
+      if (lane == 0) red[warp][c] = v;
+    }
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  const bool mine = c <= BMAX && (c < cnt || c == BMAX);
+  if (mine) {
+    W s = W(0);
+    for (int w = 0; w < NW; ++w) s += red[w][c];
+    if (CLB == 1) out[c] = s;
+    else part[ph][c] = s;
+  }
+  if constexpr (CLB > 1) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (mine) {
+      W s = W(0);
+      for (int r = 0; r < CLB; ++r) s += cl.map_shared_rank(&part[ph][0], r)[c];
+      out[c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NW, int CLB>
+__device__ __forceinline__ void batch_reduce2(double u, double v, double (*red)[2],
+                                              double (*part)[2], int ph, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u = warp_sum(u);
+  v = warp_sum(v);
+  if (lane == 0) {
+    red[warp][0] = u;
+    red[warp][1] = v;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < 2) {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += red[w][c];
+    if (CLB == 1) out[c] = s;
+    else part[ph][c] = s;
+  }
+  if constexpr (CLB > 1) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (c < 2) {
+      double s = 0.0;
+      for (int r = 0; r < CLB; ++r) s += cl.map_shared_rank(&part[ph][0], r)[c];
+      out[c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Cluster-wide barrier (global writes before it are visible to the cluster after it).
+template <int CLB>
+__device__ __forceinline__ void batch_barrier() {
+  if constexpr (CLB > 1) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
+}
+
+// Row-interleaved SpMV of the VEC rows of group gi: y[u] = sum_k a_k * src(col_k), the rows'
+// nonzeros walked in lock step so that their gathers are independent (rows >= n give 0).
+template <int VEC, class S, class W, class F>
+__device__ __forceinline__ void spmv_group(int gi, int n, const int* __restrict__ rp,
+                                           const int* __restrict__ ci, const S* __restrict__ av,
+                                           const F& src, W (&y)[VEC]) {
+  int k0[VEC], len[VEC], maxl = 0;
+#pragma unroll
+  for (int u = 0; u < VEC; ++u) {
+    const int i = gi * VEC + u;
+    k0[u] = i < n ? rp[i] : 0;
+    len[u] = i < n ? rp[i + 1] - k0[u] : 0;
+    maxl = max(maxl, len[u]);
+    y[u] = W(0);
+  }
+  for (int e = 0; e < maxl; ++e) {
+#pragma unroll
+    for (int u = 0; u < VEC; ++u)
+      if (e < len[u]) y[u] += to_w(av[k0[u] + e]) * src(ci[k0[u] + e]);
+  }
+}
+
+// Source of the first step's SpMV: the FP64 residual scaled by 1/gamma, rounded to S.
+template <class S, class W>
+struct SrcResidual {
+  const double* r;
+  double sigma;
+  __device__ __forceinline__ W operator()(int c) const { return to_w(to_s<S>(sigma * r[c])); }
+};
+// Source of the later steps: the previous step's w'' scaled by 1/||w''||, rounded to S.
+template <class S, class W>
+struct SrcWork {
+  const W* t;
+  W f;
+  __device__ __forceinline__ W operator()(int c) const { return to_w(to_s<S>(f * t[c])); }
+};
+
+// FP32: two CTAs share an SM (256 threads with up to 128 registers, or 512 threads with 64
+// and a few spills: the autotuner picks); FP64 keeps its accumulators in registers instead.
+//
+// A thread works on groups of VEC consecutive rows (one 16-byte load of a basis column per
+// group): rows 4g .. 4g+3 for FP32.  The rows of a system are split among the cluster's
+// CTAs in whole groups; rows past n in the last group are padding (zero in V, w, t).
+template <class S, class W, int NTB, int CLB>
+__global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(BatchArgs<S, W> a) {
+  constexpr int NW = NTB / 32;
+  constexpr int VEC = (int)(16 / sizeof(S));
+  __shared__ W red[NW][BMAX + 1], part[2][BMAX + 1];
+  __shared__ W h1[BMAX + 1], h2[BMAX + 1], hn[BMAX + 1];
+  __shared__ double red2[NW][2], part2[2][2], sums[2];
+  __shared__ double col[BMAX + 1], cs[BMAX], sn[BMAX], rot[BMAX], g[BMAX + 1];
+  __shared__ double Rm[BMAX * BMAX];  // R(i, c) at c * BMAX + i, i <= c
+  __shared__ W yw[BMAX];
+  __shared__ int s_q, s_done, s_k;
+  __shared__ double s_sigma;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = CLB > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  const long long ld = a.ld;
+  const size_t slot = blockIdx.x / CLB;  // the cluster's workspace
+  S* V = a.Vws + slot * (a.m + 1) * ld;
+  W* w = a.wws + slot * ld;
+  W* t = a.tws + slot * ld;
+  double* r = a.rws + slot * ld;
+  const double* b_all = a.io->b;
+  double* x_all = a.io->x;
+  int ph = 0;  // reduction phase parity (double-buffered partial sums)
+  for (;;) {
+    if (rank == 0 && tid == 0) s_q = atomicAdd(a.counter, 1);
+    batch_barrier<CLB>();
+    int q = s_q;
+    if constexpr (CLB > 1) q = *cooperative_groups::this_cluster().map_shared_rank(&s_q, 0);
+    batch_barrier<CLB>();  // rank 0 rewrites s_q only after every CTA has read it
+    if (q >= a.nsys) break;
+    const BatchSys d = a.sys[q];
+    const int n = d.n;
+    const int ngr = (n + VEC - 1) / VEC;
+    const int g0 = (int)((long long)ngr * rank / CLB), g1 = (int)((long long)ngr * (rank + 1) / CLB);
+    const int* rp = a.rp + d.row0 + d.index;
+    const int* ci = a.ci + d.nnz0;
+    const double* av64 = a.av64 + d.nnz0;
+    const S* av = a.av + d.nnz0;
+    const double* b = b_all + d.row0;
+    double* x = x_all + d.row0;
+
+    // r = b - A x (FP64), ||r||^2, ||b||^2
+    auto residual = [&]() {
+      double sr = 0.0, sb = 0.0;
+      for (int gi = g0 + tid; gi < g1; gi += NTB) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          const int i = gi * VEC + u;
+          if (i < n) {
+            double acc = 0.0;
+            for (int k = rp[i]; k < rp[i + 1]; ++k) acc += av64[k] * x[ci[k]];
+            const double bi = b[i], ri = bi - acc;
+            r[i] = ri;
+            sr += ri * ri;
+            sb += bi * bi;
+          }
+        }
+      }
+      batch_reduce2<NW, CLB>(sr, sb, red2, part2, ph, sums);
+      ph ^= 1;
+    };
+    residual();
+    const double bnorm = sqrt(sums[1]);
+    double gamma = sqrt(sums[0]);
+    long long its = 0;
+    int outer = 0, status = ST_OK;
+    if (bnorm == 0.0) {
+      for (int gi = g0 + tid; gi < g1; gi += NTB)
+        for (int u = 0; u < VEC; ++u)
+          if (gi * VEC + u < n) x[gi * VEC + u] = 0.0;
+      gamma = 0.0;
+    } else {
+      for (;;) {
+        const double rel = gamma / bnorm;
+        if (!isfinite(rel)) { status = ST_NONFINITE; break; }
+        if (rel <= a.rtol) { status = ST_OK; break; }
+        if (its >= a.max_iters) { status = ST_NOT_CONVERGED; break; }
+        // ---- one inner GMRES(m) cycle on A u = r, v_0 = r / gamma ----
+        double sigma = 1.0 / gamma;
+        if (tid == 0) g[0] = 1.0;
+        int k = 0;
+        for (int j = 0; j < a.m; ++j) {
+          W acc[BMAX + 1];
+#pragma unroll
+          for (int c = 0; c <= BMAX; ++c) acc[c] = W(0);
+          // A: v_j, w = A v_j, first-pass sums
+          const W fw = (W)sigma;
+          for (int gi = g0 + tid; gi < g1; gi += NTB) {
+            W y[VEC];
+            S vj[VEC];
+            if (j == 0) {
+              spmv_group<VEC>(gi, n, rp, ci, av, SrcResidual<S, W>{r, sigma}, y);
+#pragma unroll
+              for (int u = 0; u < VEC; ++u)
+                vj[u] = gi * VEC + u < n ? to_s<S>(sigma * r[gi * VEC + u]) : to_s<S>(0.0f);
+            } else {
+              spmv_group<VEC>(gi, n, rp, ci, av, SrcWork<S, W>{t, fw}, y);
+              W tv[VEC];
+              ldv(t + (long long)gi * VEC, tv);  // padding rows of t are zero
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) vj[u] = to_s<S>(fw * tv[u]);
+            }
+            stv(V + (long long)j * ld + (long long)gi * VEC, vj);
+            stv(w + (long long)gi * VEC, y);
+#pragma unroll
+            for (int c = 0; c < BMAX; ++c) {
+              if (c <= j) {
+                S vc[VEC];
+                if (c == j) {
+#pragma unroll
+                  for (int u = 0; u < VEC; ++u) vc[u] = vj[u];
+                } else {
+                  ldv(V + (long long)c * ld + (long long)gi * VEC, vc);
+                }
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) acc[c] += to_w(vc[u]) * y[u];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[BMAX] += y[u] * y[u];
+          }
+          batch_reduce<W, NW, CLB>(acc, j + 1, red, part, ph, h1);
+          ph ^= 1;
+          // B: w' = w - V h1, second-pass sums
+#pragma unroll
+          for (int c = 0; c <= BMAX; ++c) acc[c] = W(0);
+          for (int gi = g0 + tid; gi < g1; gi += NTB) {
+            W wv[VEC];
+            ldv(w + (long long)gi * VEC, wv);
+#pragma unroll
+            for (int c = 0; c < BMAX; ++c) {
+              if (c <= j) {
+                S vc[VEC];
+                ldv(V + (long long)c * ld + (long long)gi * VEC, vc);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) wv[u] -= h1[c] * to_w(vc[u]);
+              }
+            }
+            stv(w + (long long)gi * VEC, wv);
+            // the same thread just loaded these entries: the second read hits L1
+#pragma unroll
+            for (int c = 0; c < BMAX; ++c) {
+              if (c <= j) {
+                S vc[VEC];
+                ldv(V + (long long)c * ld + (long long)gi * VEC, vc);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) acc[c] += to_w(vc[u]) * wv[u];
+              }
+            }
+          }
+          batch_reduce<W, NW, CLB>(acc, j + 1, red, part, ph, h2);
+          ph ^= 1;
+          // C: w'' = w' - V h2 into t, ||w''||^2
+          acc[BMAX] = W(0);
+          for (int gi = g0 + tid; gi < g1; gi += NTB) {
+            W wv[VEC];
+            ldv(w + (long long)gi * VEC, wv);
+#pragma unroll
+            for (int c = 0; c < BMAX; ++c) {
+              if (c <= j) {
+                S vc[VEC];
+                ldv(V + (long long)c * ld + (long long)gi * VEC, vc);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) wv[u] -= h2[c] * to_w(vc[u]);
+              }
+            }
+            stv(t + (long long)gi * VEC, wv);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[BMAX] += wv[u] * wv[u];
+          }
+          batch_reduce<W, NW, CLB>(acc, 0, red, part, ph, hn);
+          ph ^= 1;
+          // Givens update of column j (FP64)
+          if (tid <= j) col[tid] = (double)h1[tid] + (double)h2[tid];
+          __syncthreads();
+          if (warp == 0) {
+            const double xj = givens_scan(j, col, cs, sn, rot);
+            if (lane == 0) {
+              const double hnv = sqrt((double)hn[BMAX]), wnorm = sqrt((double)h1[BMAX]);
+              double c = 1.0, s = 0.0;
+              if (hnv != 0.0) {
+                const double rho = hypot(xj, hnv);
+                c = xj / rho;
+                s = hnv / rho;
+              }
+              const double rjj = c * xj + s * hnv;
+              for (int i = 0; i < j; ++i) Rm[j * BMAX + i] = rot[i];
+              Rm[j * BMAX + j] = rjj;
+              cs[j] = c;
+              sn[j] = s;
+              const double gj = g[j];
+              g[j] = c * gj;
+              g[j + 1] = -s * gj;
+              const double res = fabs(g[j + 1]);
+              const bool bad = !isfinite(hnv) || !isfinite(res) || !isfinite(rjj);
+              const int brk = hnv <= 16.0 * a.u_work * wnorm;
+              s_done = bad ? 2 : (brk || (a.inner_rtol > 0.0 && res <= a.inner_rtol) ||
+                                  j + 1 >= a.m || its + j + 1 >= a.max_iters);
+              s_sigma = brk ? 0.0 : 1.0 / hnv;
+            }
+          }
+          __syncthreads();
+          k = j + 1;
+          sigma = s_sigma;
+          if (s_done) break;
+        }
+        if (s_done == 2) { status = ST_NONFINITE; break; }
+        // R y = g: drop trailing columns whose diagonal is negligible, back substitution
+        if (warp == 0) {
+          int kk = k;
+          double rmax = 0.0;
+          for (int c = lane; c < k; c += 32) rmax = fmax(rmax, fabs(Rm[c * BMAX + c]));
+          for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+          while (kk > 0 && !(fabs(Rm[(kk - 1) * BMAX + kk - 1]) > 16.0 * a.u_work * rmax)) --kk;
+          double gl = lane < kk ? g[lane] : 0.0, yl = 0.0;
+          for (int i = kk - 1; i >= 0; --i) {
+            const double yi = __shfl_sync(0xffffffffu, gl, i) / Rm[i * BMAX + i];
+            if (lane == i) yl = yi;
+            if (lane < i) gl -= Rm[i * BMAX + lane] * yi;
+          }
+          if (lane < BMAX) yw[lane] = lane < kk ? (W)yl : W(0);
+          if (lane == 0) s_k = kk;
+        }
+        __syncthreads();
+        const int kk = s_k;
+        // x += gamma V y (u = V y in the working precision, update in FP64)
+        for (int gi = g0 + tid; gi < g1; gi += NTB) {
+          W u[VEC];
+#pragma unroll
+          for (int q2 = 0; q2 < VEC; ++q2) u[q2] = W(0);
+          for (int c = 0; c < kk; ++c) {
+            S vc[VEC];
+            ldv(V + (long long)c * ld + (long long)gi * VEC, vc);
+#pragma unroll
+            for (int q2 = 0; q2 < VEC; ++q2) u[q2] += yw[c] * to_w(vc[q2]);
+          }
+#pragma unroll
+          for (int q2 = 0; q2 < VEC; ++q2)
+            if (gi * VEC + q2 < n) x[gi * VEC + q2] += gamma * (double)u[q2];
+        }
+        batch_barrier<CLB>();  // the residual gathers x entries of other CTAs' rows
+        its += k;
+        ++outer;
+        residual();
+        gamma = sqrt(sums[0]);
+      }
+    }
+    if (rank == 0 && tid == 0) {
+      a.status[d.index] = status;
+      a.iters[d.index] = its;
+      a.outer[d.index] = outer;
+      a.relres[d.index] = bnorm > 0.0 ? gamma / bnorm : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// Structure check of every system (one CTA per system): local row pointers from 0 to
+// nnz_i, non-decreasing, column indices in [0, n_i).
+__global__ void k_check_batch(const BatchSys* sys, int nsys, const int* rp_all, const int* ci_all,
+                              const long long* nnz_of, int* bad) {
+  for (int q = blockIdx.x; q < nsys; q += gridDim.x) {
+    const BatchSys d = sys[q];
+    const int* rp = rp_all + d.row0 + d.index;
+    const int* ci = ci_all + d.nnz0;
+    const long long nz = nnz_of[q];
+    if (threadIdx.x == 0 && (rp[0] != 0 || rp[d.n] != nz)) atomicOr(bad, 1);
+    for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
+      const int k0 = rp[i], k1 = rp[i + 1];
+      if (k1 < k0 || k0 < 0 || k1 > nz) {
+        atomicOr(bad, 1);
+        continue;
+      }
+      for (int k = k0; k < k1; ++k)
+        if ((unsigned)ci[k] >= (unsigned)d.n) atomicOr(bad, 1);
+    }
+  }
+}
+
+template <class S>
+__global__ void k_cast_batch(const double* __restrict__ v, S* __restrict__ o, long long cnt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (long long)gridDim.x * blockDim.x)
+    o[i] = to_s<S>(v[i]);
+}
+
+__global__ void k_fill(double* __restrict__ p, double v, long long cnt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  int nsys = 0, m = 0, prec = GMRES_FP32, nt = 256, clb = 1, grid = 0, tried = 0;
+  long long rows = 0, nnz = 0, ld = 0;
+  int max_n = 0;
+  gmres_params p{};
+  const int *rp = nullptr, *ci = nullptr;
+  const double* av64 = nullptr;
+  BatchSys* sys = nullptr;       // device, solve order
+  BatchSys* sys_sample = nullptr;
+  int nsample = 0;
+  int* counter = nullptr;
+  void* av = nullptr;
+  void *V = nullptr, *w = nullptr, *t = nullptr;
+  double* r = nullptr;
+  int* status = nullptr;
+  long long* iters = nullptr;
+  int* outer = nullptr;
+  double* relres = nullptr;
+  BatchIO* io = nullptr;
+  BatchIO* h_io = nullptr;       // pinned
+  int slots = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static void batch_free(BatchPlan* pl) {
+  if (!pl) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
+  if (pl->ev0) cudaEventDestroy(pl->ev0);
+  if (pl->ev1) cudaEventDestroy(pl->ev1);
+  void* ptrs[] = {pl->sys, pl->sys_sample, pl->counter, pl->av, pl->V, pl->w, pl->t, pl->r,
+                  pl->status, pl->iters, pl->outer, pl->relres, pl->io};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (pl->h_io) cudaFreeHost(pl->h_io);
+  delete pl;
+}
+
+template <int P>
+using BArgs = BatchArgs<typename Tr<P>::S, typename Tr<P>::W>;
+
+// The batched solver's inner precisions: FP64 (P = 0) and FP32 (P = 1).
+template <class F>
+static int batch_dispatch(int prec, F&& f) {
+  if (prec == GMRES_FP64) return f(std::integral_constant<int, 0>{});
+  if (prec == GMRES_FP32) return f(std::integral_constant<int, 1>{});
+  return GMRES_ERR_INVALID;
+}
+
+template <int P>
+static BArgs<P> batch_args(BatchPlan& pl, const BatchSys* sys, int nsys) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  BArgs<P> a{};
+  a.sys = sys;
+  a.nsys = nsys;
+  a.counter = pl.counter;
+  a.rp = pl.rp;
+  a.ci = pl.ci;
+  a.av64 = pl.av64;
+  a.av = (const S*)pl.av;
+  a.io = pl.io;
+  a.Vws = (S*)pl.V;
+  a.wws = (W*)pl.w;
+  a.tws = (W*)pl.t;
+  a.rws = pl.r;
+  a.ld = pl.ld;
+  a.m = pl.m;
+  a.max_iters = pl.p.max_iters;
+  a.rtol = pl.p.rtol;
+  a.inner_rtol = pl.p.inner_rtol;
+  a.u_work = P == 0 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  a.status = pl.status;
+  a.iters = pl.iters;
+  a.outer = pl.outer;
+  a.relres = pl.relres;
+  return a;
+}
+
+// The instantiated kernel for (threads per CTA, CTAs per cluster), or null.
+template <int P>
+static void* batch_kernel(int nt, int clb) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  if (nt == 256) {
+    if (clb == 1) return (void*)k_batched_ir<S, W, 256, 1>;
+    if (clb == 2) return (void*)k_batched_ir<S, W, 256, 2>;
+    if (clb == 4) return (void*)k_batched_ir<S, W, 256, 4>;
+    if (clb == 8) return (void*)k_batched_ir<S, W, 256, 8>;
+  }
+  if constexpr (P != 0) {  // 512 threads: FP32 only (FP64 would spill at 128 registers)
+    if (nt == 512) {
+      if (clb == 1) return (void*)k_batched_ir<S, W, 512, 1>;
+      if (clb == 2) return (void*)k_batched_ir<S, W, 512, 2>;
+      if (clb == 4) return (void*)k_batched_ir<S, W, 512, 4>;
+      if (clb == 8) return (void*)k_batched_ir<S, W, 512, 8>;
+    }
+  }
+  return nullptr;
+}
+
+static cudaLaunchConfig_t batch_config(int nt, int clb, int grid, cudaStream_t s,
+                                       cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)nt);
+  cfg.stream = s;
+  attr->id = cudaLaunchAttributeClusterDimension;
+  attr->val.clusterDim.x = (unsigned)clb;
+  attr->val.clusterDim.y = 1;
+  attr->val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Launches the batched kernel (counter reset + kernel) on `grid` CTAs.
+template <int P>
+static int batch_launch(BatchPlan& pl, int nt, int clb, int grid, const BatchSys* sys, int nsys,
+                        cudaStream_t s) {
+  void* k = batch_kernel<P>(nt, clb);
+  if (!k) return GMRES_ERR_INVALID;
+  BArgs<P> a = batch_args<P>(pl, sys, nsys);
+  CK(cudaMemsetAsync(pl.counter, 0, sizeof(int), s));
+  cudaLaunchAttribute attr;
+  const cudaLaunchConfig_t cfg = batch_config(nt, clb, grid, s, &attr);
+  void* args[] = {&a};
+  CK(cudaLaunchKernelExC(&cfg, k, args));
+  return GMRES_OK;
+}
+
+// CTAs that stay resident for (nt, clb): whole clusters, at most four CTAs per SM.
+template <int P>
+static int batch_grid(int nt, int clb, int sms, int* grid) {
+  void* k = batch_kernel<P>(nt, clb);
+  if (!k) return GMRES_ERR_INVALID;
+  cudaLaunchAttribute attr;
+  const cudaLaunchConfig_t cfg = batch_config(nt, clb, clb * sms, nullptr, &attr);
+  int ncl = 0;
+  CK(cudaOccupancyMaxActiveClusters(&ncl, k, &cfg));
+  if (ncl < 1) return GMRES_ERR_INVALID;
+  *grid = std::min(ncl * clb, 4 * sms) / clb * clb;
+  return GMRES_OK;
+}
+
+static int batch_create(BatchPlan** out, const gmres_csr_batch* A, const gmres_params* p,
+                        int autotune, cudaStream_t s) {
+  *out = nullptr;
+  if (!A || !p) return GMRES_ERR_INVALID;
+  if (int e = validate_params(p)) return e;
+  if (p->restart_m > GMRES_BATCH_MAX_M) return GMRES_ERR_TOO_LARGE;
+  if (p->inner_prec != GMRES_FP32 && p->inner_prec != GMRES_FP64) return GMRES_ERR_INVALID;
+  if (p->poly_degree != 0) return GMRES_ERR_INVALID;
+  if (A->nsys < 0) return GMRES_ERR_INVALID;
+  const int nsys = A->nsys;
+  if (nsys > 0 && (!A->row_off || !A->nnz_off || !A->row_ptr || !A->col_idx || !A->vals))
+    return GMRES_ERR_INVALID;
+  std::vector<BatchSys> sys(nsys);
+  std::vector<long long> nz(nsys);
+  int max_n = 0;
+  if (nsys > 0 && (A->row_off[0] != 0 || A->nnz_off[0] != 0)) return GMRES_ERR_INVALID;
+  for (int i = 0; i < nsys; ++i) {
+    const long long n = A->row_off[i + 1] - A->row_off[i], z = A->nnz_off[i + 1] - A->nnz_off[i];
+    if (n < 0 || z < 0 || n > (1LL << 30) || z > INT32_MAX) return GMRES_ERR_INVALID;
+    sys[i] = BatchSys{A->row_off[i], A->nnz_off[i], (int)n, i};
+    nz[i] = z;
+    max_n = std::max(max_n, (int)n);
+  }
+  BatchPlan* pl = new (std::nothrow) BatchPlan();
+  if (!pl) return GMRES_ERR_OOM;
+  auto fail = [&](int e) {
+    cudaStreamSynchronize(s);
+    batch_free(pl);
+    return e;
+  };
+  pl->nsys = nsys;
+  pl->m = p->restart_m;
+  pl->prec = p->inner_prec;
+  pl->p = *p;
+  pl->rows = nsys ? A->row_off[nsys] : 0;
+  pl->nnz = nsys ? A->nnz_off[nsys] : 0;
+  pl->max_n = max_n;
+  pl->ld = round_up(std::max(max_n, 1), 32);
+  pl->rp = A->row_ptr;
+  pl->ci = A->col_idx;
+  pl->av64 = A->vals;
+  if (nsys == 0) {
+    *out = pl;
+    return GMRES_OK;
+  }
+  int dev = 0, sms = 0;
+  if (int e = CUDA_STATUS(cudaGetDevice(&dev))) return fail(e);
+  if (int e = CUDA_STATUS(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return fail(e);
+  // largest systems first (ties: caller's order)
+  std::vector<BatchSys> order = sys;
+  std::stable_sort(order.begin(), order.end(), [](const BatchSys& u, const BatchSys& v) { return u.n > v.n; });
+  std::vector<long long> nz_order(nsys);
+  for (int i = 0; i < nsys; ++i) nz_order[i] = nz[order[i].index];
+  auto alloc = [&](void** q, size_t bytes) { return CUDA_STATUS(cudaMalloc(q, std::max<size_t>(bytes, 16))); };
+  int e;
+  if ((e = alloc((void**)&pl->sys, sizeof(BatchSys) * nsys))) return fail(e);
+  if ((e = alloc((void**)&pl->counter, sizeof(int)))) return fail(e);
+  if ((e = alloc((void**)&pl->status, sizeof(int) * nsys))) return fail(e);
+  if ((e = alloc((void**)&pl->iters, sizeof(long long) * nsys))) return fail(e);
+  if ((e = alloc((void**)&pl->outer, sizeof(int) * nsys))) return fail(e);
+  if ((e = alloc((void**)&pl->relres, sizeof(double) * nsys))) return fail(e);
+  if ((e = alloc((void**)&pl->io, sizeof(BatchIO)))) return fail(e);
+  if ((e = CUDA_STATUS(cudaMallocHost((void**)&pl->h_io, sizeof(BatchIO))))) return fail(e);
+  if ((e = CUDA_STATUS(cudaMemcpyAsync(pl->sys, order.data(), sizeof(BatchSys) * nsys,
+                                       cudaMemcpyHostToDevice, s))))
+    return fail(e);
+  {  // structure check (reads the caller's arrays through the descriptors)
+    long long* d_nz = nullptr;
+    int* d_bad = nullptr;
+    if ((e = alloc((void**)&d_nz, sizeof(long long) * nsys))) return fail(e);
+    if ((e = alloc((void**)&d_bad, sizeof(int)))) {
+      cudaFree(d_nz);
+      return fail(e);
+    }
+    int bad = 0;
+    e = CUDA_STATUS(cudaMemcpyAsync(d_nz, nz_order.data(), sizeof(long long) * nsys, cudaMemcpyHostToDevice, s));
+    if (!e) e = CUDA_STATUS(cudaMemsetAsync(d_bad, 0, sizeof(int), s));
+    if (!e) {
+      k_check_batch<<<std::min(nsys, 4 * sms), 256, 0, s>>>(pl->sys, nsys, pl->rp, pl->ci, d_nz, d_bad);
+      e = CUDA_STATUS(cudaGetLastError());
+    }
+    if (!e) e = CUDA_STATUS(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!e) e = CUDA_STATUS(cudaStreamSynchronize(s));
+    cudaFree(d_nz);
+    cudaFree(d_bad);
+    if (e) return fail(e);
+    if (bad) return fail(GMRES_ERR_INVALID);
+  }
+  // values in the storage precision
+  const size_t sb = storage_bytes(pl->prec), wb = work_bytes(pl->prec);
+  if ((e = alloc(&pl->av, sb * (size_t)pl->nnz))) return fail(e);
+  e = batch_dispatch(pl->prec, [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    k_cast_batch<typename Tr<P>::S><<<4 * sms, 256, 0, s>>>(pl->av64, (typename Tr<P>::S*)pl->av, pl->nnz);
+    return CUDA_STATUS(cudaGetLastError());
+  });
+  if (e) return fail(e);
+  // (CTA size, cluster size) candidates and their resident grids; the workspace holds one
+  // slot per cluster of the largest grid
+  std::vector<std::pair<int, int>> cands;
+  for (int nt : {256, 512})
+    for (int clb : {1, 2, 4, 8})
+      if (!(pl->prec == GMRES_FP64 && nt == 512)) cands.push_back({nt, clb});
+  if (!autotune) cands = {{256, 4}};
+  std::vector<int> grids(cands.size());
+  for (size_t c = 0; c < cands.size(); ++c) {
+    const int nt = cands[c].first, clb = cands[c].second;
+    e = batch_dispatch(pl->prec, [&](auto PP) { return batch_grid<decltype(PP)::value>(nt, clb, sms, &grids[c]); });
+    if (e) return fail(e);
+    grids[c] = std::min(grids[c], nsys * clb);
+    pl->slots = std::max(pl->slots, grids[c] / clb);
+  }
+  if ((e = alloc(&pl->V, sb * (size_t)pl->slots * (pl->m + 1) * pl->ld))) return fail(e);
+  if ((e = alloc(&pl->w, wb * (size_t)pl->slots * pl->ld))) return fail(e);
+  if ((e = alloc(&pl->t, wb * (size_t)pl->slots * pl->ld))) return fail(e);
+  if ((e = alloc((void**)&pl->r, 8 * (size_t)pl->slots * pl->ld))) return fail(e);
+  if ((e = CUDA_STATUS(cudaEventCreate(&pl->ev0)))) return fail(e);
+  if ((e = CUDA_STATUS(cudaEventCreate(&pl->ev1)))) return fail(e);
+  pl->nt = cands[0].first;
+  pl->clb = cands[0].second;
+  pl->grid = grids[0];
+  if (cands.size() > 1) {
+    // time each candidate on every 8th system (by size) with b = ones, x0 = 0
+    std::vector<BatchSys> sample;
+    for (int i = 0; i < nsys; i += 8) sample.push_back(order[i]);
+    pl->nsample = (int)sample.size();
+    if ((e = alloc((void**)&pl->sys_sample, sizeof(BatchSys) * sample.size()))) return fail(e);
+    double *tb = nullptr, *tx = nullptr;
+    if ((e = alloc((void**)&tb, 8 * (size_t)pl->rows))) return fail(e);
+    if ((e = alloc((void**)&tx, 8 * (size_t)pl->rows))) {
+      cudaFree(tb);
+      return fail(e);
+    }
+    auto tune = [&]() -> int {
+      CK(cudaMemcpyAsync(pl->sys_sample, sample.data(), sizeof(BatchSys) * sample.size(),
+                         cudaMemcpyHostToDevice, s));
+      k_fill<<<4 * sms, 256, 0, s>>>(tb, 1.0, pl->rows);
+      CK(cudaGetLastError());
+      pl->h_io->b = tb;
+      pl->h_io->x = tx;
+      CK(cudaMemcpyAsync(pl->io, pl->h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, s));
+      float best = 1e30f;
+      for (size_t c = 0; c < cands.size(); ++c) {
+        const int clb = cands[c].second;
+        const int gs = std::min(grids[c], (int)sample.size() * clb);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+          CK(cudaMemsetAsync(tx, 0, 8 * (size_t)pl->rows, s));
+          CK(cudaEventRecord(pl->ev0, s));
+          int e2 = batch_dispatch(pl->prec, [&](auto PP) {
+            return batch_launch<decltype(PP)::value>(*pl, cands[c].first, clb, gs, pl->sys_sample,
+                                                      (int)sample.size(), s);
+          });
+          if (e2) return e2;
+          CK(cudaEventRecord(pl->ev1, s));
+          CK(cudaEventSynchronize(pl->ev1));
+          CK(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
+        }
+        if (ms < best) {
+          best = ms;
+          pl->nt = cands[c].first;
+          pl->clb = clb;
+          pl->grid = grids[c];
+        }
+        ++pl->tried;
+      }
+      return GMRES_OK;
+    };
+    e = tune();
+    cudaStreamSynchronize(s);
+    cudaFree(tb);
+    cudaFree(tx);
+    if (e) return fail(e);
+  }
+  // the solve as a graph: counter reset + persistent kernel
+  if ((e = CUDA_STATUS(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking)))) return fail(e);
+  if ((e = CUDA_STATUS(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal)))) return fail(e);
+  e = batch_dispatch(pl->prec, [&](auto PP) {
+    return batch_launch<decltype(PP)::value>(*pl, pl->nt, pl->clb, pl->grid, pl->sys, nsys, pl->cap);
+  });
+  cudaGraph_t graph = nullptr;
+  const int e_end = CUDA_STATUS(cudaStreamEndCapture(pl->cap, &graph));
+  pl->graph = graph;
+  if (e) return fail(e);
+  if (e_end) return fail(e_end);
+  if ((e = CUDA_STATUS(cudaGraphInstantiate(&pl->exec, pl->graph, 0)))) return fail(e);
+  if ((e = CUDA_STATUS(cudaStreamSynchronize(s)))) return fail(e);
+  *out = pl;
+  return GMRES_OK;
+}
+
+static int batch_solve(BatchPlan& pl, const double* b, double* x, gmres_batch_stats* stats,
+                       cudaStream_t s) {
+  if (pl.nsys == 0) {
+    if (stats) stats->t_solve_ms = 0.0;
+    return GMRES_OK;
+  }
+  if (!b || !x) return GMRES_ERR_INVALID;
+  pl.h_io->b = b;
+  pl.h_io->x = x;
+  CK(cudaMemcpyAsync(pl.io, pl.h_io, sizeof(BatchIO), cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(pl.ev0, s));
+  CK(cudaGraphLaunch(pl.exec, s));
+  CK(cudaEventRecord(pl.ev1, s));
+  std::vector<int> st(pl.nsys);
+  CK(cudaMemcpyAsync(st.data(), pl.status, sizeof(int) * pl.nsys, cudaMemcpyDeviceToHost, s));
+  if (stats) {
+    if (stats->iters) CK(cudaMemcpyAsync(stats->iters, pl.iters, sizeof(long long) * pl.nsys, cudaMemcpyDeviceToHost, s));
+    if (stats->outer) CK(cudaMemcpyAsync(stats->outer, pl.outer, sizeof(int) * pl.nsys, cudaMemcpyDeviceToHost, s));
+    if (stats->rel_resid) CK(cudaMemcpyAsync(stats->rel_resid, pl.relres, sizeof(double) * pl.nsys, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  int first = GMRES_OK;
+  for (int i = 0; i < pl.nsys; ++i)
+    if (st[i] != GMRES_OK) {
+      first = st[i];
+      break;
+    }
+  if (stats) {
+    if (stats->status) memcpy(stats->status, st.data(), sizeof(int) * pl.nsys);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pl.ev0, pl.ev1);
+    stats->t_solve_ms = ms;
+  }
+  return first;
+}
+
+}  // namespace gm
+
+struct gmres_batch_plan_s {
+  gm::BatchPlan* pl;
+};
+
+extern "C" {
+
+int gmres_batch_plan_create(gmres_batch_plan* plan, const gmres_csr_batch* A, const gmres_params* p,
+                            int32_t autotune, void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  *plan = nullptr;
+  gm::BatchPlan* pl = nullptr;
+  const int e = gm::batch_create(&pl, A, p, autotune, (cudaStream_t)stream);
+  if (e) return e;
+  *plan = new (std::nothrow) gmres_batch_plan_s{pl};
+  if (!*plan) {
+    gm::batch_free(pl);
+    return GMRES_ERR_OOM;
+  }
+  return GMRES_OK;
+}
+
+int gmres_batch_plan_solve(gmres_batch_plan plan, const double* b, double* x, gmres_batch_stats* stats,
+                           void* stream) {
+  if (!plan || !plan->pl) return GMRES_ERR_INVALID;
+  return gm::batch_solve(*plan->pl, b, x, stats, (cudaStream_t)stream);
+}
+
+int gmres_batch_plan_info(gmres_batch_plan plan, int64_t* out) {
+  if (!plan || !plan->pl || !out) return GMRES_ERR_INVALID;
+  const gm::BatchPlan& pl = *plan->pl;
+  const int64_t v[7] = {pl.nt, pl.grid, pl.tried, pl.max_n, pl.ld, pl.prec, pl.clb};
+  memcpy(out, v, sizeof(v));
+  return GMRES_OK;
+}
+
+int gmres_batch_plan_destroy(gmres_batch_plan plan) {
+  if (!plan) return GMRES_OK;
+  gm::batch_free(plan->pl);
+  delete plan;
+  return GMRES_OK;
+}
+
+int gmres_ir_solve_batched(const gmres_csr_batch* A, const double* b, double* x, const gmres_params* p,
+                           gmres_batch_stats* stats, void* stream) {
+  gmres_batch_plan plan = nullptr;
+  int e = gmres_batch_plan_create(&plan, A, p, 0, stream);
+  if (e) return e;
+  e = gmres_batch_plan_solve(plan, b, x, stats, stream);
+  gmres_batch_plan_destroy(plan);
+  return e;
+}
+
+}  // extern "C"

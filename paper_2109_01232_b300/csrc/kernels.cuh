@@ -459,6 +459,45 @@ __device__ __forceinline__ bool cluster_column_sums(const ColF& col, int ncol, W
   return !any;
 }
 
+// Applies the rotations G_0 .. G_{js-1} (cs, sn) to the new Hessenberg column col[0..js]
+// as an affine scan (see finalize_step): writes the rotated entries rot[0..js-1] and
+// returns the rotated col[js] in every lane.  Called by all 32 lanes of one warp; col, cs,
+// sn, rot in shared memory.
+__device__ __forceinline__ double givens_scan(int js, const double* col, const double* cs,
+                                              const double* sn, double* rot) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int seg = (js + 31) / 32;
+  const int i0 = min(lane * seg, js), i1 = min(i0 + seg, js);
+  // this lane's composite map x -> A x + B over rotations [i0, i1)
+  double A = 1.0, B = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double ai = -sn[i], bi = cs[i] * col[i + 1];
+    B = fma(ai, B, bi);
+    A = ai * A;
+  }
+  // inclusive scan: lane l holds the composite of the segments of lanes 0..l
+  for (int d = 1; d < 32; d <<= 1) {
+    const double Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+    if (lane >= d) {
+      B = fma(A, Bp, B);
+      A = A * Ap;
+    }
+  }
+  const double Ae = __shfl_up_sync(full, A, 1), Be = __shfl_up_sync(full, B, 1);
+  double x = col[0];
+  if (lane > 0) x = fma(Ae, x, Be);  // x entering this lane's segment
+  for (int i = i0; i < i1; ++i) {
+    const double h = col[i + 1];
+    rot[i] = fma(cs[i], x, sn[i] * h);
+    x = fma(-sn[i], x, cs[i] * h);
+  }
+  // x_js: lane 31's composite covers every rotation
+  x = js > 0 ? fma(__shfl_sync(full, A, 31), col[0], __shfl_sync(full, B, 31)) : col[0];
+  __syncwarp();
+  return x;
+}
+
 // Shared-memory doubles that finalize_step needs (for js < LSQ_MAX).
 constexpr int GIVENS_SH = 4 * (LSQ_MAX + 2);
 
@@ -501,34 +540,7 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2,
   __shared__ int s_done;
   __shared__ double s_sigma;
   if (warp == 0) {
-    const unsigned full = 0xffffffffu;
-    const int seg = (js + 31) / 32;
-    const int i0 = min(lane * seg, js), i1 = min(i0 + seg, js);
-    // this lane's composite map x -> A x + B over rotations [i0, i1)
-    double A = 1.0, B = 0.0;
-    for (int i = i0; i < i1; ++i) {
-      const double ai = -sn[i], bi = cs[i] * col[i + 1];
-      B = fma(ai, B, bi);
-      A = ai * A;
-    }
-    // inclusive scan: lane l holds the composite of the segments of lanes 0..l
-    for (int d = 1; d < 32; d <<= 1) {
-      const double Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
-      if (lane >= d) {
-        B = fma(A, Bp, B);
-        A = A * Ap;
-      }
-    }
-    const double Ae = __shfl_up_sync(full, A, 1), Be = __shfl_up_sync(full, B, 1);
-    double x = col[0];
-    if (lane > 0) x = fma(Ae, x, Be);  // x entering this lane's segment
-    for (int i = i0; i < i1; ++i) {
-      const double h = col[i + 1];
-      rot[i] = fma(cs[i], x, sn[i] * h);
-      x = fma(-sn[i], x, cs[i] * h);
-    }
-    // x_js: the value leaving the last lane's segment (lane 31's composite covers all)
-    x = js > 0 ? fma(__shfl_sync(full, A, 31), col[0], __shfl_sync(full, B, 31)) : col[0];
+    double x = givens_scan(js, col, cs, sn, rot);
     __syncwarp();
     if (writer) {
       double* Rc = a.R + (long long)js * ldh;

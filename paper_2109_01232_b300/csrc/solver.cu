@@ -1099,3 +1099,6 @@ extern "C" int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, doub
   if (cudaGetLastError() != cudaSuccess) return GMRES_ERR_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
 }
+
+// Batched GMRES-IR (many small systems, one persistent kernel).
+#include "batched.cuh"

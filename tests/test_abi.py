@@ -90,3 +90,36 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(form), ctypes.byref(st), None) == g.ERR_INVALID
     empty = g.csr_t(0, 0, None, None, None)
     assert lib.gmres_ir_solve(ctypes.byref(empty), 1, 1, ctypes.byref(p), ctypes.byref(st), None) == g.OK
+
+
+def test_batched_arguments_rejected_before_any_launch(lib):
+    """Batched plan argument checks run on the host; an empty batch needs no device."""
+    import numpy as np
+    import paper_2109_01232_b300 as g
+    plan = ctypes.c_void_p()
+    p = g.default_params(restart_m=30)
+    empty = g.csr_batch_t(0, None, None, None, None, None)
+    assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(empty), ctypes.byref(p), 1,
+                                       None) == g.OK
+    st = g.batch_stats_t(None, None, None, None, 0.0)
+    assert lib.gmres_batch_plan_solve(plan, None, None, ctypes.byref(st), None) == g.OK
+    assert lib.gmres_batch_plan_destroy(plan) == g.OK
+    assert lib.gmres_ir_solve_batched(ctypes.byref(empty), None, None, ctypes.byref(p), None, None) == g.OK
+    ro, no = np.array([0, 4], np.int64), np.array([0, 4], np.int64)
+    one = g.csr_batch_t(1, ro.ctypes.data, no.ctypes.data, 1, 1, 1)
+    for kw, code in ((dict(restart_m=g.BATCH_MAX_M + 1), g.ERR_TOO_LARGE),
+                     (dict(inner_prec="fp16"), g.ERR_INVALID), (dict(poly_degree=3), g.ERR_INVALID)):
+        q = g.default_params(**{"restart_m": 30, **kw})
+        assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(one), ctypes.byref(q), 0,
+                                           None) == code
+    neg = g.csr_batch_t(-1, None, None, None, None, None)
+    assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(neg), ctypes.byref(p), 0,
+                                       None) == g.ERR_INVALID
+    bad_off = np.array([1, 4], np.int64)
+    shifted = g.csr_batch_t(1, bad_off.ctypes.data, no.ctypes.data, 1, 1, 1)
+    assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(shifted), ctypes.byref(p), 0,
+                                       None) == g.ERR_INVALID
+    dec = np.array([0, 4, 3], np.int64)
+    two = g.csr_batch_t(2, dec.ctypes.data, np.array([0, 4, 8], np.int64).ctypes.data, 1, 1, 1)
+    assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(two), ctypes.byref(p), 0,
+                                       None) == g.ERR_INVALID
