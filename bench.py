@@ -151,10 +151,13 @@ PROFILE_OF = {"spmv": "k_spmv_sell_3d100_fp32.md", "u1": "k_cgs_u1_3d100_fp32.md
               "u2": "k_cgs_u2_3d100_fp32.md"}
 
 
+KERNEL_SOURCES = ("common.cuh", "kernels.cuh")  # the step kernels' code
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2109_01232_b300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2109_01232_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -177,6 +180,67 @@ def measured_traffic(kernel: str, alg_bytes_avg: float):
     if fields.get("source_sha256_16") != kernel_source_hash():
         return None
     return float(fields["traffic_bytes_per_launch"]) * alg_bytes_avg / float(fields["alg_bytes_per_launch"])
+
+
+# ------------------------------------------------------- batched workload ----
+BATCH_M = 30
+
+
+def batch_cycle_bytes(n: int, nnz: int, m: int) -> float:
+    """Algorithmic bytes of one FP32 inner cycle of the batched solver on one system (the
+    per-step byte model of the single-system kernels, summed over the m steps, plus the
+    FP64 residual and the x update)."""
+    steps = sum(nnz * 8 + 4 * (n + 1) + 3 * 4 * n + j * 4 * n      # A: SpMV, v_j, w, dots
+                + (j + 1) * 4 * n + 2 * 4 * n                       # B: V once, w in/out
+                + (j + 1) * 4 * n + 2 * 4 * n for j in range(m))    # C
+    return steps + nnz * 12 + 4 * (n + 1) + 24 * n + m * 4 * n + 16 * n
+
+
+def run_batched(g, torch, peak):
+    """The batched workload: 512 independent 2D convection-diffusion systems solved by
+    GMRES-IR (FP32 inner GMRES(30)) in one persistent launch, and by FP64 GMRES(30) per
+    system in the same kernel form, on the same GPU."""
+    import gen
+    systems = gen.batched_systems()
+    batch = g.DeviceBatch([p for p, _, _ in systems])
+    b = torch.tensor(np.concatenate([bb for _, bb, _ in systems]), device="cuda")
+    x = torch.zeros_like(b)
+    t0 = time.perf_counter()
+    plan = g.BatchPlan(batch, autotune=True, restart_m=BATCH_M, rtol=RTOL)
+    tune_s = time.perf_counter() - t0
+    info = plan.info()
+    plan.solve(b, x)  # warm-up
+    ms = []
+    for _ in range(2):
+        x.zero_()
+        res = plan.solve(b, x)
+        ms.append(res.t_solve_ms)
+    plan.close()
+    if not (res.status == g.OK).all():
+        raise SystemExit("batched solve failed")
+    xs = batch.split(x.cpu().numpy())
+    err = max(float(np.abs(xi - xt).max() / np.abs(xt).max()) for xi, (_, _, xt) in zip(xs, systems))
+    plan64 = g.BatchPlan(batch, autotune=False, restart_m=BATCH_M, rtol=RTOL, inner_prec="fp64")
+    x.zero_()
+    plan64.solve(b, x)
+    x.zero_()
+    r64 = plan64.solve(b, x)
+    plan64.close()
+    t = statistics.median(ms) / 1e3
+    nbytes = sum(int(res.outer[i]) * batch_cycle_bytes(p.n, len(p.vals), BATCH_M)
+                 for i, (p, _, _) in enumerate(systems))
+    return {"workload": "512 2D convection-diffusion systems, sides U{32..256} (1,024-65,536 "
+                        "rows, 12.8M in total), Pe U(0.1, 50), b = A x_true; GMRES-IR with FP32 "
+                        "inner GMRES(30), rtol 1e-10, one persistent graph-captured launch",
+            "solves_per_s": len(systems) / t, "ms_per_batch": t * 1e3,
+            "fp64_gmres_ms_per_batch": r64.t_solve_ms,
+            "speedup_vs_fp64": r64.t_solve_ms / (t * 1e3),
+            "iters_mean": float(res.iters.mean()), "iters_max": int(res.iters.max()),
+            "max_relres": float(res.rel_resid.max()), "max_x_err_vs_x_true": err,
+            "autotuned": {"threads": info["threads"], "cluster": info["cluster"],
+                          "ctas": info["ctas"], "seconds": tune_s},
+            "hbm": {"alg_bytes": nbytes, "achieved_gbs": nbytes / t / 1e9,
+                    "frac": nbytes / t / 1e9 / peak}}
 
 
 # --------------------------------------------------------------- our arm ----
@@ -284,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
             assert r.status == g.OK
         h2d = 4 * (p.n + 1) + 12 * p.nnz + 16 * p.n
         cpu = None if args.no_cpu_baseline else cpu_baseline(it["p"], it["b"], ir_iters["pe10"])
+        batched = None if args.no_batched else run_batched(g, torch, peak)
         out = {
             "metric": METRIC, "value": per_solve_s, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -306,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
             "kernels": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv)
                             for kk, vv in v.items()} for k, v in kernels.items()},
             "cpu_baseline": cpu,
+            "batched": batched,
             "e2e": {"value": statistics.median(e2e), "unit": "s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * p.n,
                     "what": "gmres_ir_solve_host on the Pe 10 instance from pinned host memory: "
@@ -396,6 +462,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
