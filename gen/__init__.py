@@ -19,4 +19,6 @@ from .stencil import (  # noqa: F401
     batched_systems,
     selector_matrices,
     build_selector_matrix,
+    MLP_SHAPES,
+    mlp_init,
 )

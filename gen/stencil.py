@@ -221,3 +221,22 @@ def build_selector_matrix(desc: dict) -> Problem:
                             name=f"sel{desc['index']}")
     return conv_diff_3d(desc["side"], desc["peclet"], desc["wind"], desc["anisotropy"],
                         name=f"sel{desc['index']}")
+
+
+# Shape of the selector network (16 features -> 64 -> 64 -> 32 classes), needed to draw its
+# initial weights; the network's arithmetic lives in the library and in the oracle.
+MLP_SHAPES = ((16, 64), (64,), (64, 64), (64,), (64, 32), (32,))
+
+
+def mlp_init(seed: int = 4242) -> np.ndarray:
+    """Initial selector weights, flat float32 in the layout W1, b1, W2, b2, W3, b3 (W row-major
+    [in][out]): W ~ U(-a, a) with a = sqrt(6 / (fan_in + fan_out)) from PCG64(seed), b = 0."""
+    g = _rng(seed)
+    out = []
+    for s in MLP_SHAPES:
+        if len(s) == 2:
+            a = np.sqrt(6.0 / (s[0] + s[1]))
+            out.append(g.uniform(-a, a, s).astype(np.float32).ravel())
+        else:
+            out.append(np.zeros(s, np.float32))
+    return np.concatenate(out)

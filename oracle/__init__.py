@@ -21,3 +21,4 @@ from .lowprec import round_to, unit_roundoff  # noqa: F401
 from .poly import (  # noqa: F401
     splitmix64_raw, splitmix64_uniform, harmonic_ritz, leja_order, poly_roots, poly_apply,
 )
+from . import selector  # noqa: F401
