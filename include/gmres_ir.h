@@ -149,6 +149,9 @@ int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const 
 int gmres_plan_solve(gmres_plan plan, const double* b, double* x, gmres_stats* stats,
                      void* stream);
 int gmres_plan_destroy(gmres_plan plan);
+/* Changes the stopping parameters of later solves on the plan (rtol, inner_rtol,
+ * max_iters as in gmres_params); the captured cycle does not depend on them. */
+int gmres_plan_set_tolerances(gmres_plan plan, double rtol, double inner_rtol, int64_t max_iters);
 
 /* ---- Building blocks on a plan (the hot-path kernels, exposed for tests) - */
 
@@ -287,6 +290,58 @@ int gmres_batch_plan_destroy(gmres_batch_plan plan);
 /* One-shot: plan (no autotuning), solve, destroy. */
 int gmres_ir_solve_batched(const gmres_csr_batch* A, const double* b, double* x,
                            const gmres_params* p, gmres_batch_stats* stats, void* stream);
+
+/* ---- Learned parameter selector -------------------------------------------
+ * Picks the restart length, polynomial degree, inner precision and inner tolerance of
+ * GMRES-IR from 16 cheap features of A with a 16-64-64-32 MLP (ReLU, softmax over 32
+ * classes).  The paper has no such component.  Its network is trained on sweep timings of
+ * this solver (paper_2109_01232_b300/selector.py) by gmres_mlp_train; without a model, or
+ * below the model's confidence threshold, the fixed default is used: m = 50, no
+ * polynomial, FP32 inner storage, inner tolerance 1e-4. */
+#define GMRES_SEL_FEATURES 16
+#define GMRES_SEL_CLASSES 32
+#define GMRES_SEL_PARAMS 7328   /* W1[16][64] b1[64] W2[64][64] b2[64] W3[64][32] b3[32], W row-major */
+
+/* The 16 features of A (DEVICE CSR, n >= 1) into features (HOST, 16 floats), with
+ * d_i = a_ii (0 if absent), s_i = sum_j |a_ij|, lg(x) = log10(max(x, 1e-30)):
+ *  0 lg n, 1 lg nnz, 2 nnz/n, 3 max row length, 4 mean |d_i|/s_i, 5 min |d_i|/s_i,
+ *  6 share of rows with |d_i| >= s_i - |d_i|, 7 lg max s_i, 8 lg ||A||_F, 9 lg max|a_ij|,
+ *  10 lg mean |d_i|, 11 lg max|d_i| - lg min nonzero |d_i|,
+ *  12 sum (a_ij - a_ji)^2 / sum (a_ij^2 + a_ji^2) over the off-diagonal pattern,
+ *  13 mean over rows with d_i != 0 of (sum_{j != i} a_ij) / d_i,
+ *  14 log10(1 + mean |i - j| over the nonzeros), 15 log10(1 + max |i - j|).
+ * Statistics are accumulated in FP64 in a fixed order. */
+int gmres_matrix_features(const gmres_csr* A, float* features, void* stream);
+/* Class probabilities (HOST, nsamp x 32) of the rows of X (HOST, nsamp x 16, already
+ * normalised) under params (HOST, GMRES_SEL_PARAMS). */
+int gmres_mlp_forward(const float* params, const float* X, int32_t nsamp, float* probs, void* stream);
+/* Mean cross-entropy of X against labels (HOST, nsamp ints in [0, 32)) and its gradient
+ * (HOST, GMRES_SEL_PARAMS floats, the params layout). */
+int gmres_mlp_loss_grad(const float* params, const float* X, const int32_t* labels, int32_t nsamp,
+                        float* loss, float* grad, void* stream);
+/* Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8, step lr) for `epochs` steps on the
+ * device: params (HOST) in = initial weights, out = trained; losses (HOST, epochs, or
+ * NULL) = the loss before each step. */
+int gmres_mlp_train(float* params, const float* X, const int32_t* labels, int32_t nsamp,
+                    int32_t epochs, float lr, float* losses, void* stream);
+
+typedef struct {
+  const float* params;             /* HOST, GMRES_SEL_PARAMS, or NULL: always the default */
+  const float* feat_mean;          /* HOST, 16: the network's input is */
+  const float* feat_scale;         /* HOST, 16:   (feature - mean) * scale */
+  const int32_t* class_m;          /* HOST, 32: restart length of each class */
+  const int32_t* class_degree;     /* HOST, 32: polynomial degree */
+  const int32_t* class_prec;       /* HOST, 32: gmres_prec of the inner cycle */
+  const double* class_inner_rtol;  /* HOST, 32: inner tolerance */
+  float min_confidence;            /* below this top probability, use the default */
+} gmres_selector;
+
+/* Sets p->restart_m, poly_degree, inner_prec and inner_rtol for A: the selector's class
+ * if it has a model and is confident, else the default (*class_out = -1).  Other fields
+ * of p are left as they are.  confidence_out: the top class probability (0 without a
+ * model).  Either output may be NULL. */
+int gmres_select_params(const gmres_csr* A, const gmres_selector* sel, gmres_params* p,
+                        int32_t* class_out, float* confidence_out, void* stream);
 
 #ifdef __cplusplus
 }

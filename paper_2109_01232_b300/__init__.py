@@ -60,6 +60,13 @@ class csr_batch_t(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
 
 
+class selector_t(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("feat_mean", ctypes.c_void_p),
+                ("feat_scale", ctypes.c_void_p), ("class_m", ctypes.c_void_p),
+                ("class_degree", ctypes.c_void_p), ("class_prec", ctypes.c_void_p),
+                ("class_inner_rtol", ctypes.c_void_p), ("min_confidence", ctypes.c_float)]
+
+
 class batch_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("outer", ctypes.c_void_p),
                 ("rel_resid", ctypes.c_void_p), ("t_solve_ms", ctypes.c_double)]
@@ -99,6 +106,13 @@ _SIGNATURES = {
     "gmres_batch_plan_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(batch_stats_t), _P]),
     "gmres_batch_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_batch_plan_destroy": (ctypes.c_int, [_P]),
+    "gmres_matrix_features": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P]),
+    "gmres_mlp_forward": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "gmres_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
+    "gmres_mlp_train": (ctypes.c_int, [_P, _P, _P, _I32, _I32, ctypes.c_float, _P, _P]),
+    "gmres_select_params": (ctypes.c_int, [ctypes.POINTER(csr_t), ctypes.POINTER(selector_t),
+                                           ctypes.POINTER(params_t), _P, _P, _P]),
+    "gmres_plan_set_tolerances": (ctypes.c_int, [_P, _D, _D, _I64]),
     "gmres_ir_solve_batched": (ctypes.c_int, [ctypes.POINTER(csr_batch_t), _P, _P,
                                               ctypes.POINTER(params_t),
                                               ctypes.POINTER(batch_stats_t), _P]),
@@ -288,6 +302,11 @@ class Plan:
     def work_dtype(self):
         torch = _torch()
         return torch.float64 if self.prec == 0 else torch.float32
+
+    def set_tolerances(self, rtol: float, inner_rtol: float, max_iters: int):
+        _check(lib().gmres_plan_set_tolerances(self.handle, rtol, inner_rtol, max_iters),
+               "plan_set_tolerances")
+        self.params.rtol, self.params.inner_rtol, self.params.max_iters = rtol, inner_rtol, max_iters
 
     def solve(self, b, x, stream=None) -> SolveResult:
         st, hist = _stats(self.params)
@@ -481,3 +500,86 @@ def ir_solve_batched(batch: DeviceBatch, b, x, stream=None, **kw) -> BatchResult
                                         ctypes.byref(s), _stream(stream))
     _check(code, "ir_solve_batched", allowed=(OK,) + STATUS_SOLVER)
     return BatchResult(code, st, it, ou, rr, s.t_solve_ms)
+
+
+# ----------------------------------------------------------------- selector ----
+SEL_FEATURES, SEL_CLASSES, SEL_PARAMS = 16, 32, 7328
+
+
+def _f32(a, n=None):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def matrix_features(A: DeviceCSR, stream=None):
+    """The 16 selector features of A (gmres_matrix_features), float32."""
+    import numpy as np
+    out = np.zeros(SEL_FEATURES, np.float32)
+    c = A.c()
+    _check(lib().gmres_matrix_features(ctypes.byref(c), out.ctypes.data, _stream(stream)), "features")
+    return out
+
+
+def mlp_forward(params, X, stream=None):
+    import numpy as np
+    params, X = _f32(params, SEL_PARAMS), _f32(X)
+    B = X.size // SEL_FEATURES
+    out = np.zeros((B, SEL_CLASSES), np.float32)
+    _check(lib().gmres_mlp_forward(params.ctypes.data, X.ctypes.data, B, out.ctypes.data,
+                                   _stream(stream)), "mlp_forward")
+    return out
+
+
+def mlp_loss_grad(params, X, labels, stream=None):
+    import numpy as np
+    params, X = _f32(params, SEL_PARAMS), _f32(X)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    loss = np.zeros(1, np.float32)
+    grad = np.zeros(SEL_PARAMS, np.float32)
+    _check(lib().gmres_mlp_loss_grad(params.ctypes.data, X.ctypes.data, lab.ctypes.data, lab.size,
+                                     loss.ctypes.data, grad.ctypes.data, _stream(stream)), "mlp_loss_grad")
+    return float(loss[0]), grad
+
+
+def mlp_train(params0, X, labels, epochs: int, lr: float, stream=None):
+    """Full-batch Adam on the GPU (gmres_mlp_train); returns (params, losses)."""
+    import numpy as np
+    params = _f32(params0, SEL_PARAMS).copy()
+    X = _f32(X)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    losses = np.zeros(max(epochs, 1), np.float32)
+    _check(lib().gmres_mlp_train(params.ctypes.data, X.ctypes.data, lab.ctypes.data, lab.size, epochs,
+                                 float(lr), losses.ctypes.data, _stream(stream)), "mlp_train")
+    return params, losses[:epochs]
+
+
+class Selector:
+    """A trained selector model (arrays as saved by selector.save_model); None = default only."""
+
+    def __init__(self, model: dict | None):
+        import numpy as np
+        self.model = model
+        self._keep = []
+        if model is None:
+            self.c = None
+            return
+        arr = lambda k, dt: self._keep.append(np.ascontiguousarray(model[k], dtype=dt)) or self._keep[-1]
+        self.c = selector_t(arr("params", np.float32).ctypes.data, arr("feat_mean", np.float32).ctypes.data,
+                            arr("feat_scale", np.float32).ctypes.data, arr("class_m", np.int32).ctypes.data,
+                            arr("class_degree", np.int32).ctypes.data, arr("class_prec", np.int32).ctypes.data,
+                            arr("class_inner_rtol", np.float64).ctypes.data,
+                            float(model.get("min_confidence", 0.0)))
+
+    def choose(self, A: DeviceCSR, stream=None, **kw):
+        """gmres_params for A: the selector's choice (or the default) on top of kw."""
+        p = default_params(**kw)
+        cls = ctypes.c_int32(-1)
+        conf = ctypes.c_float(0.0)
+        c = A.c()
+        _check(lib().gmres_select_params(ctypes.byref(c), ctypes.byref(self.c) if self.c else None,
+                                         ctypes.byref(p), ctypes.byref(cls), ctypes.byref(conf),
+                                         _stream(stream)), "select_params")
+        return p, int(cls.value), float(conf.value)

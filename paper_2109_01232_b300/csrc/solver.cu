@@ -37,12 +37,12 @@ static int note_cuda(cudaError_t e, int line) {
 #define CK(x)                                                 \
   do {                                                        \
     cudaError_t e_ = (x);                                     \
-    if (e_ != cudaSuccess) return note_cuda(e_, __LINE__);    \
+    if (e_ != cudaSuccess) return ::gm::note_cuda(e_, __LINE__); \
   } while (0)
 // Evaluates a CUDA call; on failure records it and yields the status code, else 0.
 #define CUDA_STATUS(x) ([&]() -> int {                        \
     cudaError_t e_ = (x);                                     \
-    return e_ == cudaSuccess ? 0 : note_cuda(e_, __LINE__);   \
+    return e_ == cudaSuccess ? 0 : ::gm::note_cuda(e_, __LINE__); \
   }())
 
 static inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
@@ -814,6 +814,15 @@ int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const 
   return GMRES_OK;
 }
 
+int gmres_plan_set_tolerances(gmres_plan plan, double rtol, double inner_rtol, int64_t max_iters) {
+  if (!plan || !(rtol >= 0.0) || !(inner_rtol >= 0.0) || max_iters < 0) return GMRES_ERR_INVALID;
+  gm::Plan* pl = plan->pl;
+  pl->p.rtol = rtol;
+  pl->p.inner_rtol = inner_rtol;
+  pl->p.max_iters = max_iters;
+  return GMRES_OK;
+}
+
 int gmres_plan_destroy(gmres_plan plan) {
   if (!plan) return GMRES_ERR_INVALID;
   cudaDeviceSynchronize();
@@ -1102,3 +1111,6 @@ extern "C" int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, doub
 
 // Batched GMRES-IR (many small systems, one persistent kernel).
 #include "batched.cuh"
+
+// Learned parameter selector (features, MLP inference and training kernels).
+#include "selector.cuh"

@@ -1,0 +1,237 @@
+"""Training data, training and evaluation of the learned parameter selector.
+
+The selector (C ABI: gmres_matrix_features, gmres_mlp_*, gmres_select_params) maps 16 cheap
+features of A to one of 32 GMRES-IR configurations:
+
+    class c = (im * 4 + id) * 2 + ip,   m = (25, 50, 100, 200)[im],
+                                        poly degree = (0, 10, 25, 40)[id],
+                                        inner storage = (FP32, FP16)[ip],
+
+each with the inner tolerance (1e-2, 1e-4 or 1e-6) that was best for that class on the
+training matrices.  The fixed default -- m 50, no polynomial, FP32, inner tolerance 1e-4 --
+is the fallback and the yardstick.  Everything here drives the library through its C ABI:
+
+    sweep()        times every (class, tolerance) on each matrix with this solver
+    fit()          per-class tolerances, labels (fastest class per matrix), feature
+                   normalisation, and full-batch Adam training on the GPU (gmres_mlp_train)
+    evaluate()     held-out time ratio of the selected configuration against the default
+
+    python -m paper_2109_01232_b300.selector sweep --count 128 --first 0 --last 64 --out a.npz
+    python -m paper_2109_01232_b300.selector sweep --count 128 --first 64 --out b.npz
+    python -m paper_2109_01232_b300.selector merge a.npz b.npz     # -> selector_sweep.npz
+    python -m paper_2109_01232_b300.selector fit                   # -> selector_model.npz
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+M_VALUES = (25, 50, 100, 200)
+DEGREES = (0, 10, 25, 40)
+PRECS = ("fp32", "fp16")
+TOLS = (1e-2, 1e-4, 1e-6)
+N_CLASSES = len(M_VALUES) * len(DEGREES) * len(PRECS)
+DEFAULT = dict(m=50, degree=0, prec="fp32", inner_rtol=1e-4)
+TIMEOUT_FACTOR = 3.0  # a configuration slower than 3x the default counts as a failure
+HERE = os.path.dirname(os.path.abspath(__file__))
+MODEL_PATH = os.path.join(HERE, "selector_model.npz")
+SWEEP_PATH = os.path.join(HERE, "selector_sweep.npz")
+
+
+def class_index(im: int, idg: int, ip: int) -> int:
+    return (im * len(DEGREES) + idg) * len(PRECS) + ip
+
+
+def class_config(c: int) -> tuple[int, int, str]:
+    ip = c % len(PRECS)
+    idg = (c // len(PRECS)) % len(DEGREES)
+    im = c // (len(PRECS) * len(DEGREES))
+    return M_VALUES[im], DEGREES[idg], PRECS[ip]
+
+
+DEFAULT_CLASS = class_index(M_VALUES.index(DEFAULT["m"]), DEGREES.index(DEFAULT["degree"]),
+                            PRECS.index(DEFAULT["prec"]))
+
+
+def _solve_time(g, torch, plan, bt, x, rtol, tol, max_iters):
+    plan.set_tolerances(rtol, tol, max_iters)
+    x.zero_()
+    r = plan.solve(bt, x)
+    return (r.t_solve_ms if r.status == g.OK else np.inf), r.iters
+
+
+def sweep(descs, rtol: float = 1e-10, log=print):
+    """For each matrix descriptor (gen.selector_matrices): features, the default's time and
+    the device time (ms) of every (class, tolerance), inf for a failure or a timeout."""
+    import torch
+
+    import gen
+    import paper_2109_01232_b300 as g
+    F = np.zeros((len(descs), 16), np.float32)
+    T = np.full((len(descs), N_CLASSES, len(TOLS)), np.inf)
+    It = np.zeros((len(descs), N_CLASSES, len(TOLS)), np.int64)
+    T0 = np.zeros(len(descs))
+    for k, desc in enumerate(descs):
+        t_start = time.time()
+        p = gen.build_selector_matrix(desc)
+        A = g.DeviceCSR.from_problem(p)
+        F[k] = g.matrix_features(A)
+        bt = torch.ones(p.n, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(bt)
+        plan = g.Plan(A, "ir", restart_m=DEFAULT["m"], inner_prec=DEFAULT["prec"], rtol=rtol,
+                      inner_rtol=DEFAULT["inner_rtol"], max_iters=200000)
+        _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], 200000)  # warm-up
+        t0, it0 = _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], 200000)
+        plan.close()
+        T0[k] = t0
+        cap = int(max(200, 4 * it0)) if np.isfinite(t0) else 20000
+        for c in range(N_CLASSES):
+            m, d, prec = class_config(c)
+            try:
+                plan = g.Plan(A, "ir", restart_m=m, inner_prec=prec, poly_degree=d, rtol=rtol,
+                              max_iters=cap, seed=desc["seed"])
+            except g.GmresError:
+                continue  # e.g. a polynomial set-up that broke down: the class fails here
+            for it_, tol in enumerate(TOLS):
+                t, its = _solve_time(g, torch, plan, bt, x, rtol, tol, cap)
+                if np.isfinite(t0) and t > TIMEOUT_FACTOR * t0:
+                    t = np.inf
+                T[k, c, it_] = t
+                It[k, c, it_] = its
+            plan.close()
+        log(f"[{k + 1}/{len(descs)}] n={p.n} dim={desc['dim']} pe={desc['peclet']:.3g} "
+            f"an={desc['anisotropy']:.3g} default {t0:.1f} ms ({it0} it), best "
+            f"{np.min(T[k]):.1f} ms, {time.time() - t_start:.1f} s")
+    return dict(features=F, times=T, iters=It, default_ms=T0,
+                desc_index=np.array([d["index"] for d in descs]),
+                desc_seed=np.array([d["seed"] for d in descs]))
+
+
+def split(n: int, held_out: int, seed: int = 4999):
+    perm = np.random.Generator(np.random.PCG64(seed)).permutation(n)
+    return np.sort(perm[held_out:]), np.sort(perm[:held_out])
+
+
+def _ratio(times, t0):
+    """Time relative to the default; failures count as the timeout factor."""
+    r = times / t0
+    return np.where(np.isfinite(r), r, TIMEOUT_FACTOR)
+
+
+def fit(data: dict, train_idx, epochs: int = 3000, lr: float = 3e-3, seed: int = 4242,
+        min_confidence: float = 0.0):
+    """Per-class tolerances, labels and GPU training (gmres_mlp_train) on train_idx."""
+    import gen
+    import paper_2109_01232_b300 as g
+    T, T0, F = data["times"][train_idx], data["default_ms"][train_idx], data["features"][train_idx]
+    ok = np.isfinite(T0)
+    T, T0, F = T[ok], T0[ok], F[ok]
+    # each class keeps the tolerance with the smallest geometric-mean time ratio
+    tol_idx = np.zeros(N_CLASSES, int)
+    for c in range(N_CLASSES):
+        gm = [np.exp(np.mean(np.log(_ratio(T[:, c, t], T0)))) for t in range(len(TOLS))]
+        tol_idx[c] = int(np.argmin(gm))
+    Tc = np.stack([T[:, c, tol_idx[c]] for c in range(N_CLASSES)], axis=1)
+    labels = np.argmin(np.where(np.isfinite(Tc), Tc, np.inf), axis=1)
+    labels[~np.isfinite(Tc).any(axis=1)] = DEFAULT_CLASS
+    mean = F.mean(axis=0)
+    std = F.std(axis=0)
+    scale = np.where(std > 1e-6, 1.0 / np.maximum(std, 1e-6), 0.0).astype(np.float32)
+    X = ((F - mean) * scale).astype(np.float32)
+    params, losses = g.mlp_train(gen.mlp_init(seed), X, labels, epochs, lr)
+    cm = np.array([class_config(c)[0] for c in range(N_CLASSES)], np.int32)
+    cd = np.array([class_config(c)[1] for c in range(N_CLASSES)], np.int32)
+    cp = np.array([g.PREC[class_config(c)[2]] for c in range(N_CLASSES)], np.int32)
+    ct = np.array([TOLS[tol_idx[c]] for c in range(N_CLASSES)], np.float64)
+    return dict(params=params, feat_mean=mean.astype(np.float32), feat_scale=scale,
+                class_m=cm, class_degree=cd, class_prec=cp, class_inner_rtol=ct,
+                min_confidence=np.float32(min_confidence), train_labels=labels.astype(np.int32),
+                train_losses=losses, tol_index=tol_idx)
+
+
+def predict(model: dict, F) -> tuple[np.ndarray, np.ndarray]:
+    """Chosen class (or -1 = default) and confidence for feature rows F (GPU forward)."""
+    import paper_2109_01232_b300 as g
+    X = ((np.asarray(F, np.float32) - model["feat_mean"]) * model["feat_scale"]).astype(np.float32)
+    P = g.mlp_forward(model["params"], X)
+    c = P.argmax(axis=1)
+    conf = P.max(axis=1)
+    c = np.where(conf >= float(model["min_confidence"]), c, -1)
+    return c, conf
+
+
+def evaluate(data: dict, model: dict, idx) -> dict:
+    """Time of the selected configuration relative to the default on the matrices idx."""
+    c, conf = predict(model, data["features"][idx])
+    T, T0 = data["times"][idx], data["default_ms"][idx]
+    chosen = np.array([T0[k] if c[k] < 0 else T[k, c[k], model["tol_index"][c[k]]]
+                       for k in range(len(idx))])
+    ok_def = np.isfinite(T0)
+    r = _ratio(chosen[ok_def], T0[ok_def])
+    # the best any single class could do with its stored tolerance (the oracle choice)
+    best = np.array([min(T[k, cc, model["tol_index"][cc]] for cc in range(N_CLASSES))
+                     for k in range(len(idx))])
+    return dict(geomean_ratio=float(np.exp(np.mean(np.log(r)))),
+                converged_selected=int(np.isfinite(chosen).sum()),
+                converged_default=int(ok_def.sum()), n=len(idx),
+                best_possible_geomean=float(np.exp(np.mean(np.log(_ratio(best[ok_def], T0[ok_def]))))),
+                chosen=c)
+
+
+def save(path: str, d: dict):
+    np.savez_compressed(path, **{k: np.asarray(v) for k, v in d.items()})
+
+
+def load(path: str) -> dict:
+    with np.load(path) as f:
+        return {k: f[k] for k in f.files}
+
+
+def main(argv=None):
+    sys.path.insert(0, os.path.dirname(HERE))
+    import gen
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    s1 = sub.add_parser("sweep")
+    s1.add_argument("--count", type=int, default=128)
+    s1.add_argument("--n-hi", type=float, default=2e5)
+    s1.add_argument("--first", type=int, default=0, help="sweep matrices [first, last) only")
+    s1.add_argument("--last", type=int, default=None)
+    s1.add_argument("--out", default=SWEEP_PATH)
+    s3 = sub.add_parser("merge")
+    s3.add_argument("parts", nargs="+")
+    s3.add_argument("--out", default=SWEEP_PATH)
+    s2 = sub.add_parser("fit")
+    s2.add_argument("--sweep", default=SWEEP_PATH)
+    s2.add_argument("--held-out", type=float, default=0.2)
+    s2.add_argument("--out", default=MODEL_PATH)
+    a = ap.parse_args(argv)
+    if a.cmd == "sweep":
+        descs = gen.selector_matrices(count=a.count, n_hi=a.n_hi)[a.first:a.last]
+        data = sweep(descs)
+        data["n_hi"] = np.float64(a.n_hi)
+        save(a.out, data)
+    elif a.cmd == "merge":
+        parts = [load(q) for q in a.parts]
+        data = {k: np.concatenate([q[k] for q in parts]) for k in parts[0] if k != "n_hi"}
+        order = np.argsort(data["desc_index"], kind="stable")
+        data = {k: v[order] for k, v in data.items()}
+        data["n_hi"] = parts[0]["n_hi"]
+        save(a.out, data)
+    else:
+        data = load(a.sweep)
+        n = len(data["default_ms"])
+        tr, te = split(n, int(round(a.held_out * n)))
+        model = fit(data, tr)
+        model["held_out"] = te
+        res = evaluate(data, model, te)
+        print({k: v for k, v in res.items() if k != "chosen"})
+        save(a.out, model)
+
+
+if __name__ == "__main__":
+    main()
