@@ -21,4 +21,9 @@ from .stencil import (  # noqa: F401
     build_selector_matrix,
     MLP_SHAPES,
     mlp_init,
+    stencil_matrix,
+    laplace_2d,
+    laplace_3d,
+    box_2d,
+    star_3d,
 )

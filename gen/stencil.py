@@ -240,3 +240,55 @@ def mlp_init(seed: int = 4242) -> np.ndarray:
         else:
             out.append(np.zeros(s, np.float32))
     return np.concatenate(out)
+
+
+def stencil_matrix(dims: tuple[int, ...], offsets, name: str) -> Problem:
+    """Constant-coefficient stencil on a grid with zero Dirichlet boundary: -1 for every
+    in-grid neighbour at the given offsets and the stencil's neighbour count on the diagonal
+    (a Galeri-style Laplacian of any stencil shape).  Rows in lexicographic order, x fastest."""
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    idx = np.arange(n)
+    coords = np.unravel_index(idx, dims[::-1])[::-1]  # coords[0] = x (fastest)
+    strides = [int(np.prod(dims[:k])) for k in range(len(dims))]
+    rows, cols, vals = [idx], [idx], [np.zeros(n)]
+    for off in offsets:
+        ok = np.ones(n, bool)
+        shift = 0
+        for k, o in enumerate(off):
+            c = coords[k] + o
+            ok &= (c >= 0) & (c < dims[k])
+            shift += o * strides[k]
+        r = idx[ok]
+        rows.append(r)
+        cols.append(r + shift)
+        vals.append(-np.ones(len(r)))
+    vals[0] = np.full(n, float(len(offsets)))
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    A.sort_indices()
+    return Problem(name, n, A.indptr.astype(np.int32), A.indices.astype(np.int32),
+                   A.data.astype(np.float64), dict(dims=list(dims), stencil=len(offsets) + 1))
+
+
+def laplace_2d(side: int) -> Problem:
+    """5-point Laplacian (Galeri Laplace2D-like)."""
+    return stencil_matrix((side, side), [(1, 0), (-1, 0), (0, 1), (0, -1)], f"laplace2d_{side}")
+
+
+def laplace_3d(side: int) -> Problem:
+    """7-point Laplacian (Galeri Laplace3D-like)."""
+    offs = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    return stencil_matrix((side, side, side), offs, f"laplace3d_{side}")
+
+
+def box_2d(side: int) -> Problem:
+    """9-point box stencil (Galeri Star2D / Cross-like 3x3 neighbourhood)."""
+    offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+    return stencil_matrix((side, side), offs, f"box2d_{side}")
+
+
+def star_3d(side: int) -> Problem:
+    """13-point fourth-order star: two neighbours along each axis direction in 3D."""
+    offs = [tuple(s * r if k == a else 0 for k in range(3)) for a in range(3) for s in (1, -1)
+            for r in (1, 2)]
+    return stencil_matrix((side, side, side), offs, f"star3d_{side}")

@@ -82,6 +82,10 @@ typedef struct {
   uint64_t seed;            /* SplitMix64 seed of the polynomial's start vector */
   int32_t record_history;   /* nonzero: keep |g_{j+1}| per iteration in gmres_stats */
   int32_t cgs_kernel;       /* gmres_cgs_kernel: how the CGS2 update kernels read V */
+  int32_t poly_in_fp32;     /* nonzero: apply the polynomial preconditioner in FP32 (an FP32
+                               copy of A, FP32 vectors, cast in and out) under an FP64 cycle --
+                               the paper's FP64 GMRES with an FP32 polynomial (Section 5.4);
+                               ignored when the cycle is not FP64 */
 } gmres_params;
 
 /* Forms of the two CGS2 update kernels (the same arithmetic per row; both produce the
@@ -130,6 +134,17 @@ int gmres_solve(const gmres_csr* A, const double* b, double* x, const gmres_para
 int gmres_ir_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
                    gmres_stats* stats, void* stream);
 
+/* GMRES-FD (Section 3.3): restarted GMRES(m) entirely in single precision (b, A, x, the
+ * basis and the explicit residual rounded to FP32, FP32 arithmetic) for switch_iters
+ * iterations, rounded up to whole cycles so that the switch happens at a restart, then
+ * FP64 GMRES(m) (as gmres_solve) from that iterate for the remaining p->max_iters.
+ * Pointers as in gmres_solve.  stats_fp32 / stats_fp64 (either may be NULL) describe the
+ * two stages; the return value is the FP64 stage's status.  switch_iters = 0 is plain
+ * FP64 GMRES; no polynomial preconditioner (p->poly_degree must be 0). */
+int gmres_fd_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                   int64_t switch_iters, gmres_stats* stats_fp32, gmres_stats* stats_fp64,
+                   void* stream);
+
 /* Same solves with HOST pointers: A's arrays, b and x live in host memory
  * (pinned memory gives the fastest copies).  The call copies A, b and x0 to
  * the device, solves, and copies x back before returning. */
@@ -142,13 +157,21 @@ int gmres_solve_host(const gmres_csr* A_host, const double* b, double* x,
  * and the captured CUDA graph of one cycle between solves. ----------------- */
 typedef struct gmres_plan_s* gmres_plan;
 
-/* kind: 0 = FP64 GMRES, 1 = GMRES-IR with p->inner_prec.  A's arrays must stay
+/* kind: 0 = FP64 GMRES, 1 = GMRES-IR with p->inner_prec, 2 = GMRES entirely in FP32
+ * (GMRES-FD's first stage; p->inner_prec ignored, no polynomial).  A's arrays must stay
  * valid until gmres_plan_destroy. */
 int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const gmres_params* p,
                       void* stream);
 int gmres_plan_solve(gmres_plan plan, const double* b, double* x, gmres_stats* stats,
                      void* stream);
 int gmres_plan_destroy(gmres_plan plan);
+/* Times y = A x with the plan's SELL-32 inner copy of A, the SpMV alone (no dot products,
+ * no basis store; Section 5.5's fp64-vs-fp32 experiment): one warm-up launch, then `reps`
+ * launches between CUDA events on `stream`.  x, y: DEVICE, n values of the plan's working
+ * type (double for FP64 plans, float otherwise), not overlapping.  *ms_out = mean ms per
+ * SpMV. */
+int gmres_plan_spmv_timed(gmres_plan plan, const void* x, void* y, int32_t reps, float* ms_out,
+                          void* stream);
 /* Changes the stopping parameters of later solves on the plan (rtol, inner_rtol,
  * max_iters as in gmres_params); the captured cycle does not depend on them. */
 int gmres_plan_set_tolerances(gmres_plan plan, double rtol, double inner_rtol, int64_t max_iters);
@@ -180,8 +203,8 @@ int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const do
 /* y = p(A) v with the plan's GMRES polynomial (Section 3.4; the plan must have
  * poly_degree > 0): the product form over the Leja-ordered roots, d SpMVs with
  * the plan's inner copy of A, in the working precision.  v: DEVICE, n doubles;
- * y: DEVICE, n values of the working type (double for FP64 plans, float
- * otherwise). */
+ * y: DEVICE, n values of the polynomial's working type (double for FP64 plans,
+ * float otherwise and for FP64 plans created with poly_in_fp32). */
 int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream);
 
 /* The plan's polynomial roots (HOST arrays of at least poly_degree+1 entries,

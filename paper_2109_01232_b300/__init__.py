@@ -44,7 +44,7 @@ class params_t(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("inner_prec", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32),
-                ("cgs_kernel", ctypes.c_int32)]
+                ("cgs_kernel", ctypes.c_int32), ("poly_in_fp32", ctypes.c_int32)]
 
 
 class stats_t(ctypes.Structure):
@@ -106,6 +106,8 @@ _SIGNATURES = {
     "gmres_batch_plan_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(batch_stats_t), _P]),
     "gmres_batch_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_batch_plan_destroy": (ctypes.c_int, [_P]),
+    "gmres_fd_solve": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, ctypes.POINTER(params_t), _I64,
+                                      ctypes.POINTER(stats_t), ctypes.POINTER(stats_t), _P]),
     "gmres_matrix_features": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P]),
     "gmres_mlp_forward": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "gmres_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P, _P]),
@@ -113,6 +115,7 @@ _SIGNATURES = {
     "gmres_select_params": (ctypes.c_int, [ctypes.POINTER(csr_t), ctypes.POINTER(selector_t),
                                            ctypes.POINTER(params_t), _P, _P, _P]),
     "gmres_plan_set_tolerances": (ctypes.c_int, [_P, _D, _D, _I64]),
+    "gmres_plan_spmv_timed": (ctypes.c_int, [_P, _P, _P, _I32, _P, _P]),
     "gmres_ir_solve_batched": (ctypes.c_int, [ctypes.POINTER(csr_batch_t), _P, _P,
                                               ctypes.POINTER(params_t),
                                               ctypes.POINTER(batch_stats_t), _P]),
@@ -280,13 +283,14 @@ def gmres_solve_host(row_ptr, col_idx, vals, b, x, stream=None, **kw) -> SolveRe
 class Plan:
     """Reusable solver workspace + captured cycle graph for one matrix.
 
-    kind: 'gmres' (FP64 GMRES) or 'ir' (GMRES-IR with inner_prec)."""
+    kind: 'gmres' (FP64 GMRES), 'ir' (GMRES-IR with inner_prec) or 'fp32' (GMRES entirely
+    in single precision, GMRES-FD's first stage)."""
 
     def __init__(self, A: DeviceCSR, kind: str = "ir", stream=None, **kw):
         self.A = A
         self.params = default_params(**kw)
-        self.kind = {"gmres": 0, "ir": 1}[kind]
-        self.prec = 0 if self.kind == 0 else self.params.inner_prec
+        self.kind = {"gmres": 0, "ir": 1, "fp32": 2}[kind]
+        self.prec = 0 if self.kind == 0 else (1 if self.kind == 2 else self.params.inner_prec)
         h = ctypes.c_void_p()
         c = A.c()
         _check(lib().gmres_plan_create(ctypes.byref(h), ctypes.byref(c), self.kind,
@@ -302,6 +306,16 @@ class Plan:
     def work_dtype(self):
         torch = _torch()
         return torch.float64 if self.prec == 0 else torch.float32
+
+    def spmv_timed(self, x, reps: int = 1000, stream=None):
+        """(y = A x, mean ms per SpMV) with the plan's inner copy of A alone; x in the working
+        dtype."""
+        torch = _torch()
+        y = torch.empty(self.A.n, dtype=self.work_dtype, device="cuda")
+        ms = ctypes.c_float(0.0)
+        _check(lib().gmres_plan_spmv_timed(self.handle, _ptr(x), _ptr(y), int(reps), ctypes.byref(ms),
+                                           _stream(stream)), "spmv_timed")
+        return y, float(ms.value)
 
     def set_tolerances(self, rtol: float, inner_rtol: float, max_iters: int):
         _check(lib().gmres_plan_set_tolerances(self.handle, rtol, inner_rtol, max_iters),
@@ -331,9 +345,10 @@ class Plan:
         return V, H.T.copy(), int(k.value)
 
     def poly_apply(self, v, stream=None):
-        """y = p(A) v with the plan's GMRES polynomial (working dtype)."""
+        """y = p(A) v with the plan's GMRES polynomial (the polynomial's working dtype)."""
         torch = _torch()
-        y = torch.empty(self.A.n, dtype=self.work_dtype, device="cuda")
+        dt = torch.float32 if (self.prec == 0 and self.params.poly_in_fp32) else self.work_dtype
+        y = torch.empty(self.A.n, dtype=dt, device="cuda")
         _check(lib().gmres_plan_poly_apply(self.handle, _ptr(v), _ptr(y), _stream(stream)),
                "poly_apply")
         return y
@@ -583,3 +598,18 @@ class Selector:
                                          ctypes.byref(p), ctypes.byref(cls), ctypes.byref(conf),
                                          _stream(stream)), "select_params")
         return p, int(cls.value), float(conf.value)
+
+
+def gmres_fd_solve(A: DeviceCSR, b, x, switch_iters: int, stream=None, **kw):
+    """GMRES-FD (Section 3.3): FP32 GMRES for switch_iters iterations (rounded up to whole
+    cycles), then FP64 GMRES from that iterate.  Returns (fp32 stage, fp64 stage) results."""
+    p = default_params(**kw)
+    s32, h32 = _stats(p)
+    s64, h64 = _stats(p)
+    c = A.c()
+    code = lib().gmres_fd_solve(ctypes.byref(c), _ptr(b), _ptr(x), ctypes.byref(p), int(switch_iters),
+                                ctypes.byref(s32), ctypes.byref(s64), _stream(stream))
+    r64 = _result(code, s64, h64)
+    r32 = SolveResult(int(s32.status), int(s32.iters), int(s32.outer_iters), float(s32.rel_resid),
+                      float(s32.t_solve_ms), float(s32.t_setup_ms))
+    return r32, r64

@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -70,12 +71,12 @@ __device__ __forceinline__ void tile_spmv(const int* __restrict__ rp, const int*
       const int ca = ci[e], cb = ci[e + NT], cc = ci[e + 2 * NT], cd = ci[e + 3 * NT];
       const AT aa = av[e], ab = av[e + NT], ac = av[e + 2 * NT], ad = av[e + 3 * NT];
       const W xa = xval(ca), xb = xval(cb), xc = xval(cc), xd = xval(cd);
-      prod_s[e - c0] = to_w(aa) * xa;
-      prod_s[e + NT - c0] = to_w(ab) * xb;
-      prod_s[e + 2 * NT - c0] = to_w(ac) * xc;
-      prod_s[e + 3 * NT - c0] = to_w(ad) * xd;
+      prod_s[e - c0] = (W)to_w(aa) * xa;
+      prod_s[e + NT - c0] = (W)to_w(ab) * xb;
+      prod_s[e + 2 * NT - c0] = (W)to_w(ac) * xc;
+      prod_s[e + 3 * NT - c0] = (W)to_w(ad) * xd;
     }
-    for (; e < c1; e += NT) prod_s[e - c0] = to_w(av[e]) * xval(ci[e]);
+    for (; e < c1; e += NT) prod_s[e - c0] = (W)to_w(av[e]) * xval(ci[e]);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
@@ -924,7 +925,9 @@ __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) 
 // x += gamma * V y (the correction u = V y accumulates in the working precision,
 // the update is FP64: Algorithm 2, "x_{i+1} = x_i + u_i [double]").
 // ---------------------------------------------------------------------------
-template <int P>
+// F32: x kept in single precision (x = fl32(fl32(x) + fl32(gamma) u)), for GMRES-FD's first
+// stage; otherwise x += gamma u in FP64.
+template <int P, bool F32 = false>
 __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict__ V, long long ld,
                                              double v_scale, DevState* st,
                                              const double* __restrict__ y, double* __restrict__ x) {
@@ -964,7 +967,10 @@ __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict
     double xv[VEC];
     ldv(x + base, xv);
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) xv[q] += fac * (double)u[q];
+    for (int q = 0; q < VEC; ++q) {
+      if constexpr (F32) xv[q] = (double)((float)xv[q] + (float)fac * (float)u[q]);
+      else xv[q] += fac * (double)u[q];
+    }
     stv(x + base, xv);
   }
 }
@@ -978,37 +984,42 @@ constexpr int RES_TR = NT * 2;
 constexpr int RES_CAP = 4096;  // nonzeros staged per chunk (32 KB)
 inline size_t residual_smem() { return sizeof(double) * RES_CAP + sizeof(int) * (RES_TR + 1) + 16; }
 
+// F32: the residual of GMRES run entirely in single precision (GMRES-FD's first stage,
+// Section 3.3): b, A and x rounded to FP32 and the products and sums in FP32; the result
+// is stored in the FP64 vector r and its norms accumulated in FP64.
+template <bool F32>
 __global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, const int* __restrict__ ci,
                                                  const double* __restrict__ av, int n,
                                                  const double* __restrict__ x,
                                                  const double* __restrict__ b, double* __restrict__ r,
                                                  double* __restrict__ part, DevState* st, Arrays arr,
                                                  int first) {
+  using RW = typename std::conditional<F32, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* prod_s = reinterpret_cast<double*>(smem_raw);
-  int* rp_s = reinterpret_cast<int*>(prod_s + RES_CAP);
+  RW* prod_s = reinterpret_cast<RW*>(smem_raw);
+  int* rp_s = reinterpret_cast<int*>(smem_raw + sizeof(double) * RES_CAP);
   __shared__ double red_r[NWARP], red_b[NWARP];
   __shared__ int s_skip, s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_skip = read_flag(&st->stop);
   __syncthreads();
   if (s_skip) return;
-  auto xval = [&](int c) -> double { return x[c]; };
+  auto xval = [&](int c) -> RW { return (RW)x[c]; };
   double sr = 0.0, sb = 0.0;
   const int ntiles = (n + RES_TR - 1) / RES_TR;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int r0 = t * RES_TR;
-    double a[RES_TR / NT];
-    tile_spmv<double, double, RES_TR, RES_CAP>(rp, ci, av, n, r0, rp_s, prod_s, xval, a);
+    RW a[RES_TR / NT];
+    tile_spmv<double, RW, RES_TR, RES_CAP>(rp, ci, av, n, r0, rp_s, prod_s, xval, a);
 #pragma unroll
     for (int k = 0; k < RES_TR / NT; ++k) {
       const int row = r0 + tid + k * NT;
       if (row < n) {
-        const double bv = b[row];
-        const double rv = bv - a[k];
-        r[row] = rv;
-        sr += rv * rv;
-        sb += bv * bv;
+        const RW bv = (RW)b[row];
+        const RW rv = bv - a[k];
+        r[row] = (double)rv;
+        sr += (double)rv * (double)rv;
+        sb += (double)bv * (double)bv;
       }
     }
   }

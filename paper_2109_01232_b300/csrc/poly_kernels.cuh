@@ -27,10 +27,12 @@ __device__ __forceinline__ int poly_skip(const DevState* st, int in_cycle) {
 // stores it: see k_spmv_sell),
 // which gives 1 / h_{j,j-1}; then V[:, j] = store(v_scale * sigma * src) (the
 // normalisation of the previous step) and prod = v_j in the working type.
-template <int P, class SrcT>
+// PW: type of prod (the polynomial's working type; FP32 under an FP64 cycle when the
+// polynomial is applied in single precision).
+template <int P, class SrcT, class PW = typename Tr<P>::W>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(const SrcT* __restrict__ src, double v_scale,
                                                    int n, typename Tr<P>::S* V, long long ld,
-                                                   int j, typename Tr<P>::W* __restrict__ prod,
+                                                   int j, PW* __restrict__ prod,
                                                    StepParts<typename Tr<P>::W> parts,
                                                    DevState* st, Arrays arr) {
   using S = typename Tr<P>::S;
@@ -61,7 +63,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(co
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
     const S v = to_s<S>(f * src[i]);
     Vj[i] = v;
-    prod[i] = to_w(v) * inv;
+    prod[i] = (PW)(to_w(v) * inv);
   }
 }
 
@@ -113,6 +115,33 @@ __global__ void __launch_bounds__(NT) k_poly_spmv(
   }
 }
 
+// y = A x with the plan's SELL-32 copy alone (no dot products, no basis store): the SpMV
+// of the fp64-vs-fp32 timing entry point (Section 5.5's experiment).
+template <int P>
+__global__ void __launch_bounds__(NT) k_spmv_plain(const int2* __restrict__ meta, const int* __restrict__ ci,
+                                                   const typename Tr<P>::S* __restrict__ av, int nslices,
+                                                   int n, double a_scale,
+                                                   const typename Tr<P>::W* __restrict__ x,
+                                                   typename Tr<P>::W* __restrict__ y) {
+  using S = typename Tr<P>::S;
+  using W = typename Tr<P>::W;
+  constexpr int TR = SpmvSmem<P>::TR;
+  constexpr int RPT = TR / NT;
+  const W as = (W)a_scale;
+  auto xval = [&](int c) -> W { return x[c]; };
+  const int ntiles = (n + TR - 1) / TR;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r0 = t * TR;
+    W a[RPT];
+    sell_rows<S, W, RPT>(meta, ci, av, nslices, r0, xval, a);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int row = r0 + threadIdx.x + k * NT;
+      if (row < n) y[row] = as * a[k];
+    }
+  }
+}
+
 // Last real root: y = y0 + c1 prod (no matrix product).
 template <int P>
 __global__ void __launch_bounds__(NT) k_poly_axpy(const typename Tr<P>::W* __restrict__ prod,
@@ -131,11 +160,10 @@ __global__ void __launch_bounds__(NT) k_poly_axpy(const typename Tr<P>::W* __res
 
 // Cycle end with a preconditioner: prod = (V y_ls) / v_scale in the working type
 // (the correction before p(A) is applied).
-template <int P>
+template <int P, class UW = typename Tr<P>::W>
 __global__ void __launch_bounds__(NT) k_vy(const typename Tr<P>::S* __restrict__ V, long long ld,
                                            double v_scale, const DevState* st,
-                                           const double* __restrict__ y,
-                                           typename Tr<P>::W* __restrict__ u) {
+                                           const double* __restrict__ y, UW* __restrict__ u) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
@@ -167,15 +195,14 @@ __global__ void __launch_bounds__(NT) k_vy(const typename Tr<P>::S* __restrict__
       for (int q = 0; q < VEC; ++q) acc[q] += k0 * to_w(v0[q]);
     }
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) acc[q] *= inv;
-    stv(u + base, acc);
+    for (int q = 0; q < VEC; ++q) u[base + q] = (UW)(acc[q] * inv);
   }
 }
 
 // x += gamma * z (FP64 update of Algorithm 2 with the preconditioned correction z).
-template <int P>
-__global__ void __launch_bounds__(NT) k_xadd(const typename Tr<P>::W* __restrict__ z,
-                                             double* __restrict__ x, int n, const DevState* st) {
+template <class ZW>
+__global__ void __launch_bounds__(NT) k_xadd(const ZW* __restrict__ z, double* __restrict__ x, int n,
+                                             const DevState* st) {
   __shared__ int s_skip;
   __shared__ double s_g;
   if (threadIdx.x == 0) {

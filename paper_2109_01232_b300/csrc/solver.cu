@@ -87,6 +87,8 @@ struct Plan {
   std::vector<double> roots_re, roots_im;
   std::vector<PolyOp> poly;         // product-form program built from the roots
   void *pa = nullptr, *pb = nullptr, *pt = nullptr, *py = nullptr;  // working-type vectors
+  bool poly32 = false;           // FP64 cycle, polynomial applied in FP32
+  void* sell_vals32 = nullptr;   // FP32 values of the SELL copy (poly32)
   int grid_elem = 1;
   double t_setup_ms = 0.0;
 };
@@ -140,6 +142,8 @@ template <int P>
 static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
+  // P is the polynomial's precision: the plan's, or FP32 under an FP64 cycle (poly32)
+  const void* vals = pl.poly32 && P == 1 ? pl.sell_vals32 : pl.sell_vals;
   W* cur = (W*)pl.pa;
   W* nxt = (W*)pl.pb;
   W* y = (W*)pl.py;
@@ -151,19 +155,19 @@ static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
         k_poly_axpy<P><<<pl.grid_elem, NT, 0, s>>>(cur, y, pl.n, op.c1, first, pl.st, in_cycle);
       } else {
         k_poly_spmv<P, POLY_REAL><<<pl.grid_spmv, NT, 0, s>>>(
-            pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+            pl.sell_meta, pl.sell_cols, (const S*)vals, pl.nslices, pl.n, pl.a_scale, cur,
             nullptr, y, nxt,
             op.c1, 0.0, first, pl.st, in_cycle);
         std::swap(cur, nxt);
       }
     } else {
       k_poly_spmv<P, POLY_PAIR_A><<<pl.grid_spmv, NT, 0, s>>>(
-          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+          pl.sell_meta, pl.sell_cols, (const S*)vals, pl.nslices, pl.n, pl.a_scale, cur,
           nullptr, y,
           op.last ? nullptr : t, op.c1, op.c2, first, pl.st, in_cycle);
       if (!op.last) {
         k_poly_spmv<P, POLY_PAIR_B><<<pl.grid_spmv, NT, 0, s>>>(
-            pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.a_scale, cur,
+            pl.sell_meta, pl.sell_cols, (const S*)vals, pl.nslices, pl.n, pl.a_scale, cur,
             t, nullptr, nxt,
             op.c1, op.c2, 0, pl.st, in_cycle);
         std::swap(cur, nxt);
@@ -187,6 +191,19 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   const StepParts<W> sp = step_parts<P>(pl);
   if (which == 0) {
     const size_t sm1 = SellSmem<P>::bytes(j + 2);
+    if (!pl.poly.empty() && pl.poly32) {  // FP64 cycle, polynomial in FP32
+      if (j == 0)
+        k_poly_start<P, double, float><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
+                                                                  (float*)pl.pa, sp, pl.st, pl.arr);
+      else
+        k_poly_start<P, W, float><<<pl.grid_elem, NT, 0, s>>>(w3, pl.v_scale, pl.n, V, pl.ld, j,
+                                                             (float*)pl.pa, sp, pl.st, pl.arr);
+      launch_poly<1>(pl, 1, s);
+      k_spmv_sell<P, float, true><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, pl.a_scale,
+          (const float*)pl.py, pl.v_scale, V, j, w1, sp, pl.st, pl.arr);
+      return;
+    }
     if (!pl.poly.empty()) {
       if (j == 0)
         k_poly_start<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
@@ -238,9 +255,14 @@ static void launch_step(Plan& pl, int j, cudaStream_t s) {
 }
 
 static void launch_residual(Plan& pl, int first, cudaStream_t s) {
-  k_residual<<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals, pl.n,
-                                                       pl.xb, pl.bb, pl.r, (double*)pl.part, pl.st,
-                                                       pl.arr, first);
+  if (pl.kind == 2)  // single-precision GMRES: FP32 residual
+    k_residual<true><<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals,
+                                                             pl.n, pl.xb, pl.bb, pl.r, (double*)pl.part,
+                                                             pl.st, pl.arr, first);
+  else
+    k_residual<false><<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals,
+                                                              pl.n, pl.xb, pl.bb, pl.r, (double*)pl.part,
+                                                              pl.st, pl.arr, first);
 }
 
 // Kernel `which` of the cycle's end (0: least squares, 1: x update -- x += gamma p(A) V y
@@ -256,13 +278,24 @@ static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
                                                                                    packed);
   } else if (which == 1) {
     if (!pl.poly.empty()) {
-      k_vy<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
-                                                               pl.st, pl.arr.y, (W*)pl.pa);
-      launch_poly<P>(pl, 0, s);
-      k_xadd<P><<<pl.grid_elem, NT, 0, s>>>((const W*)pl.py, pl.xb, pl.n, pl.st);
+      if (pl.poly32) {
+        k_vy<P, float><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>(
+            (const S*)pl.V, pl.ld, pl.v_scale, pl.st, pl.arr.y, (float*)pl.pa);
+        launch_poly<1>(pl, 0, s);
+        k_xadd<float><<<pl.grid_elem, NT, 0, s>>>((const float*)pl.py, pl.xb, pl.n, pl.st);
+      } else {
+        k_vy<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
+                                                                 pl.st, pl.arr.y, (W*)pl.pa);
+        launch_poly<P>(pl, 0, s);
+        k_xadd<W><<<pl.grid_elem, NT, 0, s>>>((const W*)pl.py, pl.xb, pl.n, pl.st);
+      }
     } else {
-      k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld,
-                                                                 pl.v_scale, pl.st, pl.arr.y, pl.xb);
+      if (pl.kind == 2)
+        k_xupd<P, true><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld,
+                                                                         pl.v_scale, pl.st, pl.arr.y, pl.xb);
+      else
+        k_xupd<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld,
+                                                                   pl.v_scale, pl.st, pl.arr.y, pl.xb);
     }
   } else {
     launch_residual(pl, 0, s);
@@ -310,6 +343,8 @@ static int configure(Plan& pl) {
                           (int)sm_attr));
   CK(cudaFuncSetAttribute(k_spmv_sell<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_attr));
+  CK(cudaFuncSetAttribute(k_spmv_sell<P, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_attr));
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
   CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)(sizeof(W) * (size_t)(LSQ_MAX + 1) * (1 + NWARP))));
@@ -334,7 +369,7 @@ static int configure(Plan& pl) {
 
 static int configure_residual(Plan& pl) {
   int occ = 1;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual, NT, residual_smem()));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<false>, NT, residual_smem()));
   const long long ntiles = (pl.n + RES_TR - 1) / RES_TR;
   pl.grid_res = (int)std::max(1LL, std::min(ntiles, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
   return GMRES_OK;
@@ -373,6 +408,7 @@ static void plan_free(Plan* pl) {
   cudaFree(pl->bb);
   cudaFree(pl->part);
   cudaFree(pl->pa);
+  cudaFree(pl->sell_vals32);
   cudaFree(pl->pb);
   cudaFree(pl->pt);
   cudaFree(pl->py);
@@ -417,7 +453,8 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   *out = nullptr;
   if (int e = validate_csr(A)) return e;
   if (int e = validate_params(p)) return e;
-  if (kind != 0 && kind != 1) return GMRES_ERR_INVALID;
+  if (kind < 0 || kind > 2) return GMRES_ERR_INVALID;
+  if (kind == 2 && p->poly_degree != 0) return GMRES_ERR_INVALID;  // FP32 GMRES: no polynomial
   if (A->n == 0) return GMRES_ERR_INVALID;  // an empty system has no plan (solves return OK)
   Plan* pl = new (std::nothrow) Plan();
   if (!pl) return GMRES_ERR_OOM;
@@ -427,7 +464,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     return e;
   };
   pl->kind = kind;
-  pl->prec = kind == 0 ? GMRES_FP64 : p->inner_prec;
+  pl->prec = kind == 0 ? GMRES_FP64 : kind == 2 ? GMRES_FP32 : p->inner_prec;
   pl->A = *A;
   pl->n = A->n;
   pl->m = p->restart_m;
@@ -549,10 +586,19 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     pl->roots_re.assign(re.begin(), re.begin() + nr);
     pl->roots_im.assign(im.begin(), im.begin() + nr);
     pl->poly = poly_program(pl->roots_re, pl->roots_im);
-    if ((e = alloc(&pl->pa, wb * (size_t)ld))) return fail(e);
-    if ((e = alloc(&pl->pb, wb * (size_t)ld))) return fail(e);
-    if ((e = alloc(&pl->pt, wb * (size_t)ld))) return fail(e);
-    if ((e = alloc(&pl->py, wb * (size_t)ld))) return fail(e);
+    pl->poly32 = p->poly_in_fp32 != 0 && pl->prec == GMRES_FP64;
+    const size_t pwb = pl->poly32 ? 4 : wb;
+    if (pl->poly32) {  // FP32 copy of the SELL values for the polynomial
+      if ((e = alloc(&pl->sell_vals32, 4 * (size_t)std::max(pl->sell_nnz, 1LL)))) return fail(e);
+      k_build_sell<float><<<pl->sms * 8, 256, 0, s>>>(A->row_ptr, A->col_idx, A->vals, pl->n,
+                                                     pl->sell_meta, pl->nslices, 1.0, pl->sell_cols,
+                                                     (float*)pl->sell_vals32);
+      if (int e_ = CUDA_STATUS(cudaGetLastError())) return fail(e_);
+    }
+    if ((e = alloc(&pl->pa, pwb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->pb, pwb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->pt, pwb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->py, pwb * (size_t)ld))) return fail(e);
     if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
     pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
   }
@@ -576,7 +622,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
 static void init_state(Plan& pl, DevState& h) {
   memset(&h, 0, sizeof(h));
   h.m = pl.m;
-  h.mode = pl.kind == 0 ? 0 : 1;
+  h.mode = pl.kind == 1 ? 1 : 0;  // GMRES (FP64 or FP32) ends a cycle at the tolerance
   h.max_iters = pl.p.max_iters;
   h.rtol = pl.p.rtol;
   h.inner_rtol = pl.p.inner_rtol;
@@ -638,7 +684,8 @@ int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
   if (pl.poly.empty() || !v || !y) return GMRES_ERR_INVALID;
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  int e = dispatch(pl.prec, [&](auto PP) {
+  // the polynomial's precision: the plan's, or FP32 for an FP64 plan with poly_in_fp32
+  int e = dispatch(pl.poly32 ? GMRES_FP32 : pl.prec, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using W = typename Tr<P>::W;
     k_load_work<P><<<pl.grid_elem, NT, 0, s>>>(v, (W*)pl.pa, pl.n);
@@ -823,6 +870,33 @@ int gmres_plan_set_tolerances(gmres_plan plan, double rtol, double inner_rtol, i
   return GMRES_OK;
 }
 
+int gmres_plan_spmv_timed(gmres_plan plan, const void* x, void* y, int32_t reps, float* ms_out,
+                          void* stream) {
+  if (!plan || !x || !y || reps < 1 || !ms_out) return GMRES_ERR_INVALID;
+  gm::Plan& pl = *plan->pl;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = pl.grid_spmv;
+  auto launch = [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    using S = typename gm::Tr<P>::S;
+    using W = typename gm::Tr<P>::W;
+    gm::k_spmv_plain<P><<<grid, gm::NT, 0, s>>>(pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals,
+                                                pl.nslices, pl.n, pl.a_scale, (const W*)x, (W*)y);
+    return 0;
+  };
+  gm::dispatch(pl.prec, launch);  // warm-up
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(pl.ev0, s));
+  for (int r = 0; r < reps; ++r) gm::dispatch(pl.prec, launch);
+  CK(cudaEventRecord(pl.ev1, s));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(pl.ev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, pl.ev0, pl.ev1));
+  *ms_out = ms / (float)reps;
+  return GMRES_OK;
+}
+
 int gmres_plan_destroy(gmres_plan plan) {
   if (!plan) return GMRES_ERR_INVALID;
   cudaDeviceSynchronize();
@@ -913,6 +987,30 @@ int gmres_solve(const gmres_csr* A, const double* b, double* x, const gmres_para
 int gmres_ir_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
                    gmres_stats* stats, void* stream) {
   return solve_once(A, b, x, p, 1, stats, stream);
+}
+
+int gmres_fd_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
+                   int64_t switch_iters, gmres_stats* stats_fp32, gmres_stats* stats_fp64,
+                   void* stream) {
+  if (int e = gm::validate_params(p)) return e;
+  if (switch_iters < 0 || p->poly_degree != 0) return GMRES_ERR_INVALID;
+  // the switch happens at a restart: round up to whole cycles of the FP32 stage
+  const int64_t m = p->restart_m;
+  gmres_params q = *p;
+  q.max_iters = std::min<int64_t>(p->max_iters, (switch_iters + m - 1) / m * m);
+  int e = GMRES_OK;
+  int64_t used = 0;
+  if (q.max_iters > 0) {
+    e = solve_once(A, b, x, &q, 2, stats_fp32, stream);
+    if (e != GMRES_OK && e != GMRES_NOT_CONVERGED && e != GMRES_BREAKDOWN) return e;
+    if (stats_fp32) used = stats_fp32->iters;
+    else used = q.max_iters;
+  } else if (stats_fp32) {
+    memset(stats_fp32, 0, sizeof(*stats_fp32));
+  }
+  q = *p;
+  q.max_iters = std::max<int64_t>(0, p->max_iters - used);
+  return solve_once(A, b, x, &q, 0, stats_fp64, stream);
 }
 
 static int solve_host(const gmres_csr* Ah, const double* b, double* x, const gmres_params* p, int kind,

@@ -166,3 +166,22 @@ def test_poly_roots_match_oracle(g, torch):
         res = np.linalg.norm(v0 - op(oracle.poly_apply(op, r_dev, v0))) / np.linalg.norm(v0)
         res_o = np.linalg.norm(v0 - op(oracle.poly_apply(op, r_ora, v0))) / np.linalg.norm(v0)
         assert res == pytest.approx(res_o, rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_plain_spmv_parity(g, torch, prec):
+    """The SpMV-only timing kernel computes the same product as the oracle."""
+    p = PROBLEMS["3d"]()
+    A, plan = _plan(g, p, prec)
+    v = np.random.default_rng(2).uniform(-1.0, 1.0, p.n)
+    x = torch.tensor(v, device="cuda", dtype=torch.float64 if prec == "fp64" else torch.float32)
+    y, ms = plan.spmv_timed(x, 3)
+    pm = oracle.Precision.for_inner(prec, p)
+    a_low = pm.matrix_values(p.vals)
+    xv = x.double().cpu().numpy()
+    y_ref = pm.s_A * oracle.spmv(p, xv, a_low)
+    absA = pm.s_A * oracle.spmv(p, np.abs(xv), np.abs(a_low))
+    tol = 1e-13 if prec == "fp64" else 1e-5
+    assert np.all(np.abs(y.double().cpu().numpy() - y_ref) <= tol * absA + 1e-300)
+    assert ms > 0
+    plan.close()

@@ -88,3 +88,31 @@ def test_preconditioned_solves(g, torch, kind, prec):
         if prec == "fp32":
             _, io = oracle.gmres_ir(p, b, m=30, rtol=1e-10, poly_roots=th, inner="fp32")
             assert abs(r.iters - io.iters) <= 60
+
+
+def test_fp64_gmres_with_fp32_polynomial(g, torch):
+    """FP64 GMRES with the polynomial applied in FP32 (Section 5.4's middle configuration):
+    the apply matches the emulated FP32 oracle, and the solve reaches 1e-10 in about the
+    iterations of the all-FP64 preconditioned solve."""
+    p, b = gen.config_aniso_2d(side=64)
+    A = g.DeviceCSR.from_problem(p)
+    plan = g.Plan(A, "gmres", restart_m=30, poly_degree=10, seed=7, poly_in_fp32=1)
+    v = np.random.default_rng(5).uniform(-1, 1, p.n)
+    z = plan.poly_apply(torch.tensor(v, device="cuda"))
+    assert z.dtype == torch.float32
+    pm = oracle.Precision.for_inner("fp32", p)
+    a_low = pm.matrix_values(p.vals)
+    op_low = lambda x: pm.rw(pm.s_A * oracle.spmv(p, x, a_low))
+    th = oracle.poly_roots(lambda x: oracle.spmv(p, x), p.n, 10, seed=7)
+    zo = oracle.poly_apply(op_low, th, pm.rw(v), pm.rw)
+    assert np.linalg.norm(z.double().cpu().numpy() - zo) <= 1e-5 * np.linalg.norm(zo)
+    plan.close()
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    r = g.gmres_solve(A, bt, xt, restart_m=30, rtol=1e-10, poly_degree=10, seed=7, poly_in_fp32=1,
+                      max_iters=20000)
+    x = xt.cpu().numpy()
+    relres = np.linalg.norm(b - oracle.spmv(p, x)) / np.linalg.norm(b)
+    assert r.status == g.OK and relres <= 1.0001e-10
+    r64 = g.gmres_solve(A, bt, xt.zero_(), restart_m=30, rtol=1e-10, poly_degree=10, seed=7,
+                        max_iters=20000)
+    assert abs(r.iters - r64.iters) <= 30
