@@ -358,15 +358,9 @@ __global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(Batc
           __syncthreads();
           if (warp == 0) {
             const double xj = givens_scan(j, col, cs, sn, rot);
+            const GivensRot gr = givens_rotation(xj, (double)hn[BMAX], (double)h1[BMAX]);
             if (lane == 0) {
-              const double hnv = sqrt((double)hn[BMAX]), wnorm = sqrt((double)h1[BMAX]);
-              double c = 1.0, s = 0.0;
-              if (hnv != 0.0) {
-                const double rho = hypot(xj, hnv);
-                c = xj / rho;
-                s = hnv / rho;
-              }
-              const double rjj = c * xj + s * hnv;
+              const double hnv = gr.hn, wnorm = gr.wnorm, c = gr.c, s = gr.s, rjj = gr.rjj;
               for (int i = 0; i < j; ++i) Rm[j * BMAX + i] = rot[i];
               Rm[j * BMAX + j] = rjj;
               cs[j] = c;
@@ -379,7 +373,7 @@ __global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(Batc
               const int brk = hnv <= 16.0 * a.u_work * wnorm;
               s_done = bad ? 2 : (brk || (a.inner_rtol > 0.0 && res <= a.inner_rtol) ||
                                   j + 1 >= a.m || its + j + 1 >= a.max_iters);
-              s_sigma = brk ? 0.0 : 1.0 / hnv;
+              s_sigma = brk ? 0.0 : gr.inv_hn;
             }
           }
           __syncthreads();

@@ -111,6 +111,42 @@ __device__ __forceinline__ bool arrive_last(unsigned int* ticket, int* s_last) {
 // every load of values and column indices is one coalesced 128-byte access and a row
 // needs no shared memory or barrier.  Computes the rows r0 + tid + k*NT (k < RPT).
 // ---------------------------------------------------------------------------
+// acc[k] += sum over the entries e < mt[k].y of slice k's row `lane`: value * xval(column),
+// in entry order.  EB entries of all R slices are loaded (indices and values) before any
+// gather and the gathers before any product, so 2 R EB loads and then R EB gathers are in
+// flight per lane; padding entries (value 0, a valid column) need no test.
+template <int EB, class AT, class W, int R, class XF>
+__device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, const int* __restrict__ sc,
+                                                const AT* __restrict__ sv, int lane, const XF& xval,
+                                                W (&acc)[R]) {
+  for (int e0 = 0; e0 < maxw; e0 += EB) {
+    int ci[EB][R];
+    AT va[EB][R];
+#pragma unroll
+    for (int eb = 0; eb < EB; ++eb) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const bool ok = e0 + eb < mt[k].y;
+        const int idx = mt[k].x + (e0 + eb) * 32 + lane;
+        ci[eb][k] = ok ? sc[idx] : -1;
+        va[eb][k] = ok ? sv[idx] : AT(0);
+      }
+    }
+    W xv[EB][R];
+#pragma unroll
+    for (int eb = 0; eb < EB; ++eb) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) xv[eb][k] = ci[eb][k] >= 0 ? xval(ci[eb][k]) : W(0);
+    }
+#pragma unroll
+    for (int eb = 0; eb < EB; ++eb) {
+#pragma unroll
+      for (int k = 0; k < R; ++k)
+        if (ci[eb][k] >= 0) acc[k] += to_w(va[eb][k]) * xv[eb][k];
+    }
+  }
+}
+
 template <class AT, class W, int RPT, class XF>
 __device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const int* __restrict__ sc,
                                           const AT* __restrict__ sv, int nslices, int r0,
@@ -126,16 +162,7 @@ __device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const i
     maxw = max(maxw, mt[k].y);
     acc[k] = W(0);
   }
-#pragma unroll 4
-  for (int e = 0; e < maxw; ++e) {
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      if (e < mt[k].y) {
-        const int idx = mt[k].x + e * 32 + lane;
-        acc[k] += to_w(sv[idx]) * xval(sc[idx]);
-      }
-    }
-  }
+  sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, acc);
 }
 
 // Sum of the G per-CTA partials p[0..G) by one warp, four independent load streams per
@@ -499,6 +526,34 @@ __device__ __forceinline__ double givens_scan(int js, const double* col, const d
   return x;
 }
 
+// The new Givens rotation of a column whose rotated diagonal entry is x and whose
+// subdiagonal is hn = sqrt(hn2), with wnorm = sqrt(wn2) for the breakdown test.  Called by
+// all 32 lanes of a warp (every lane gets the results): the two square roots share one
+// FP64 instruction (lanes 0 and 1), and c = x / rho, s = hn / rho and 1 / hn share one
+// division (lanes 0, 1, 2) -- FP64 is slow on a B300, and these sit on every step's path.
+// (c, s) = (1, 0) when hn == 0.
+struct GivensRot {
+  double c, s, rjj, hn, wnorm, inv_hn;
+};
+__device__ __forceinline__ GivensRot givens_rotation(double x, double hn2, double wn2) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const double sq = sqrt(lane == 0 ? hn2 : (lane == 1 ? wn2 : 1.0));
+  GivensRot g;
+  g.hn = __shfl_sync(full, sq, 0);
+  g.wnorm = __shfl_sync(full, sq, 1);
+  const double rho = hypot(x, g.hn);
+  const double num = lane == 0 ? x : (lane == 1 ? g.hn : 1.0);
+  const double den = lane <= 1 ? rho : g.hn;
+  const double q = num / den;
+  const double qc = __shfl_sync(full, q, 0), qs = __shfl_sync(full, q, 1);
+  g.inv_hn = __shfl_sync(full, q, 2);
+  g.c = g.hn != 0.0 ? qc : 1.0;
+  g.s = g.hn != 0.0 ? qs : 0.0;
+  g.rjj = g.c * x + g.s * g.hn;
+  return g;
+}
+
 // Shared-memory doubles that finalize_step needs (for js < LSQ_MAX).
 constexpr int GIVENS_SH = 4 * (LSQ_MAX + 2);
 
@@ -541,28 +596,22 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2,
   __shared__ int s_done;
   __shared__ double s_sigma;
   if (warp == 0) {
-    double x = givens_scan(js, col, cs, sn, rot);
+    const double x = givens_scan(js, col, cs, sn, rot);
+    const GivensRot gr = givens_rotation(x, hn2, wn2);
     __syncwarp();
     if (writer) {
       double* Rc = a.R + (long long)js * ldh;
       for (int i = lane; i < js; i += 32) Rc[i] = rot[i];
     }
     if (lane == 0) {
-      const double hn = sqrt(hn2), wnorm = sqrt(wn2);
-      double c = 1.0, s = 0.0;
-      if (hn != 0.0) {
-        const double rho = hypot(x, hn);
-        c = x / rho;
-        s = hn / rho;
-      }
-      const double rjj = c * x + s * hn;
+      const double hn = gr.hn, wnorm = gr.wnorm, c = gr.c, s = gr.s, rjj = gr.rjj;
       const double res = a.gabs[js] * fabs(s);
       const long long iters = st->iters0 + js + 1;
       const bool bad = !isfinite(hn) || !isfinite(res) || !isfinite(rjj);
       const int brk = hn <= 16.0 * st->u_work * wnorm;
       const int done = bad || brk || res <= st->stop_rel || js + 1 >= st->m || iters >= st->max_iters;
       s_done = done;
-      s_sigma = brk ? 0.0 : 1.0 / hn;
+      s_sigma = brk ? 0.0 : gr.inv_hn;
       if (writer) {
         double* Hc = a.H + (long long)js * ldh;
         double* Rc = a.R + (long long)js * ldh;
@@ -677,16 +726,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     W a[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) a[q] = W(0);
-#pragma unroll 4
-    for (int e = 0; e < maxw; ++e) {
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) {
-        if (e < mt[q].y) {
-          const int idx = mt[q].x + e * 32 + lane;
-          a[q] += to_w(sv[idx]) * xval(sc[idx]);
-        }
-      }
-    }
+    sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, a);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       const int row = r0 + 32 * q + lane;

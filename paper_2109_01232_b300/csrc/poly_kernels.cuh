@@ -73,7 +73,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(co
 //   POLY_PAIR_B: s = A tin;   out = prod - c1 tin + c2 s
 // y0 = 0 when `first`, else the current y.  in_cycle: also skip once the cycle ended.
 template <int P, int KIND>
-__global__ void __launch_bounds__(NT) k_poly_spmv(
+__global__ void __launch_bounds__(NT, 2) k_poly_spmv(
     const int2* __restrict__ meta, const int* __restrict__ ci,
     const typename Tr<P>::S* __restrict__ av, int nslices,
     int n, double a_scale, const typename Tr<P>::W* __restrict__ prod,
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(NT) k_poly_spmv(
 // y = A x with the plan's SELL-32 copy alone (no dot products, no basis store): the SpMV
 // of the fp64-vs-fp32 timing entry point (Section 5.5's experiment).
 template <int P>
-__global__ void __launch_bounds__(NT) k_spmv_plain(const int2* __restrict__ meta, const int* __restrict__ ci,
+__global__ void __launch_bounds__(NT, 2) k_spmv_plain(const int2* __restrict__ meta, const int* __restrict__ ci,
                                                    const typename Tr<P>::S* __restrict__ av, int nslices,
                                                    int n, double a_scale,
                                                    const typename Tr<P>::W* __restrict__ x,

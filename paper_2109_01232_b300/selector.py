@@ -37,6 +37,7 @@ TOLS = (1e-2, 1e-4, 1e-6)
 N_CLASSES = len(M_VALUES) * len(DEGREES) * len(PRECS)
 DEFAULT = dict(m=50, degree=0, prec="fp32", inner_rtol=1e-4)
 TIMEOUT_FACTOR = 3.0  # a configuration slower than 3x the default counts as a failure
+DEFAULT_CAP = 20000   # iterations of the default run (a longer default counts as not converged)
 HERE = os.path.dirname(os.path.abspath(__file__))
 MODEL_PATH = os.path.join(HERE, "selector_model.npz")
 SWEEP_PATH = os.path.join(HERE, "selector_sweep.npz")
@@ -64,9 +65,10 @@ def _solve_time(g, torch, plan, bt, x, rtol, tol, max_iters):
     return (r.t_solve_ms if r.status == g.OK else np.inf), r.iters
 
 
-def sweep(descs, rtol: float = 1e-10, log=print):
+def sweep(descs, rtol: float = 1e-10, log=print, checkpoint: str | None = None):
     """For each matrix descriptor (gen.selector_matrices): features, the default's time and
-    the device time (ms) of every (class, tolerance), inf for a failure or a timeout."""
+    the device time (ms) of every (class, tolerance), inf for a failure or a timeout.  With
+    `checkpoint`, the matrices done so far are saved there after each one."""
     import torch
 
     import gen
@@ -83,22 +85,33 @@ def sweep(descs, rtol: float = 1e-10, log=print):
         bt = torch.ones(p.n, dtype=torch.float64, device="cuda")
         x = torch.zeros_like(bt)
         plan = g.Plan(A, "ir", restart_m=DEFAULT["m"], inner_prec=DEFAULT["prec"], rtol=rtol,
-                      inner_rtol=DEFAULT["inner_rtol"], max_iters=200000)
-        _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], 200000)  # warm-up
-        t0, it0 = _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], 200000)
+                      inner_rtol=DEFAULT["inner_rtol"], max_iters=DEFAULT_CAP)
+        _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], DEFAULT_CAP)  # warm-up
+        t0, it0 = _solve_time(g, torch, plan, bt, x, rtol, DEFAULT["inner_rtol"], DEFAULT_CAP)
+        if not np.isfinite(t0):  # the default did not converge: time its capped run instead
+            plan.set_tolerances(rtol, DEFAULT["inner_rtol"], DEFAULT_CAP)
+            x.zero_()
+            t_ref = plan.solve(bt, x).t_solve_ms
+        else:
+            t_ref = t0
         plan.close()
         T0[k] = t0
-        cap = int(max(200, 4 * it0)) if np.isfinite(t0) else 20000
         for c in range(N_CLASSES):
             m, d, prec = class_config(c)
             try:
                 plan = g.Plan(A, "ir", restart_m=m, inner_prec=prec, poly_degree=d, rtol=rtol,
-                              max_iters=cap, seed=desc["seed"])
+                              max_iters=m, seed=desc["seed"])
             except g.GmresError:
                 continue  # e.g. a polynomial set-up that broke down: the class fails here
+            # iteration cap from the time of one cycle, so no run lasts much over the timeout
+            plan.set_tolerances(rtol, TOLS[0], m)
+            x.zero_()
+            rp_ = plan.solve(bt, x)
+            per_it = rp_.t_solve_ms / max(rp_.iters, 1)
+            cap = int(min(DEFAULT_CAP, max(m, 1.2 * TIMEOUT_FACTOR * t_ref / max(per_it, 1e-6)) + m))
             for it_, tol in enumerate(TOLS):
                 t, its = _solve_time(g, torch, plan, bt, x, rtol, tol, cap)
-                if np.isfinite(t0) and t > TIMEOUT_FACTOR * t0:
+                if t > TIMEOUT_FACTOR * t_ref:
                     t = np.inf
                 T[k, c, it_] = t
                 It[k, c, it_] = its
@@ -106,9 +119,15 @@ def sweep(descs, rtol: float = 1e-10, log=print):
         log(f"[{k + 1}/{len(descs)}] n={p.n} dim={desc['dim']} pe={desc['peclet']:.3g} "
             f"an={desc['anisotropy']:.3g} default {t0:.1f} ms ({it0} it), best "
             f"{np.min(T[k]):.1f} ms, {time.time() - t_start:.1f} s")
-    return dict(features=F, times=T, iters=It, default_ms=T0,
-                desc_index=np.array([d["index"] for d in descs]),
-                desc_seed=np.array([d["seed"] for d in descs]))
+        if checkpoint:
+            save(checkpoint, _sweep_dict(F, T, It, T0, descs, k + 1))
+    return _sweep_dict(F, T, It, T0, descs, len(descs))
+
+
+def _sweep_dict(F, T, It, T0, descs, done: int) -> dict:
+    return dict(features=F[:done], times=T[:done], iters=It[:done], default_ms=T0[:done],
+                desc_index=np.array([d["index"] for d in descs[:done]]),
+                desc_seed=np.array([d["seed"] for d in descs[:done]]))
 
 
 def split(n: int, held_out: int, seed: int = 4999):
@@ -122,7 +141,7 @@ def _ratio(times, t0):
     return np.where(np.isfinite(r), r, TIMEOUT_FACTOR)
 
 
-def fit(data: dict, train_idx, epochs: int = 3000, lr: float = 3e-3, seed: int = 4242,
+def fit(data: dict, train_idx, epochs: int = 1000, lr: float = 3e-3, seed: int = 4242,
         min_confidence: float = 0.0):
     """Per-class tolerances, labels and GPU training (gmres_mlp_train) on train_idx."""
     import gen
@@ -212,7 +231,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "sweep":
         descs = gen.selector_matrices(count=a.count, n_hi=a.n_hi)[a.first:a.last]
-        data = sweep(descs)
+        data = sweep(descs, checkpoint=a.out)
         data["n_hi"] = np.float64(a.n_hi)
         save(a.out, data)
     elif a.cmd == "merge":
