@@ -321,6 +321,12 @@ def gmres(A, b, x0=None, m: int = 50, rtol: float = 1e-10, max_iters: int = 1000
     return x, info
 
 
+# GMRES-IR gives up (NOT_CONVERGED) after this many refinement steps in a row that do not
+# lower the explicit relative residual by 0.1%: with an inner precision too coarse for the
+# problem the refinement stalls or diverges (the paper does not say when to stop then).
+IR_STALL_LIMIT = 20
+
+
 def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32",
              inner_rtol: float = 0.0, max_iters: int = 100000, poly_roots=None,
              arith: str = "fp32") -> tuple[np.ndarray, Info]:
@@ -351,13 +357,14 @@ def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32
     r = b - spmv(A, x)  # [double]
     gamma = float(np.linalg.norm(r))
     info = Info(OK, 0, 0, gamma / bnorm, [gamma / bnorm])
+    best, stall = gamma / bnorm, 0  # stall test (reading: no 0.1% progress in 20 steps)
     while True:
         if not np.isfinite(gamma):
             info.status = NONFINITE
             break
         if gamma <= rtol * bnorm:
             break
-        if info.iters >= max_iters:
+        if info.iters >= max_iters or stall >= IR_STALL_LIMIT:
             info.status = NOT_CONVERGED
             break
         cyc = gmres_cycle(op, r, min(m, max_iters - info.iters), inner_rtol, prec)  # [single]
@@ -373,6 +380,10 @@ def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32
         gamma = float(np.linalg.norm(r))
         info.relres = gamma / bnorm
         info.history.append(info.relres)
+        if info.relres < best * (1.0 - 1e-3):
+            best, stall = info.relres, 0
+        else:
+            stall += 1
         if cyc.singular:
             info.status = BREAKDOWN if gamma > rtol * bnorm else OK
             break

@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(Batc
     const double bnorm = sqrt(sums[1]);
     double gamma = sqrt(sums[0]);
     long long its = 0;
-    int outer = 0, status = ST_OK;
+    int outer = 0, status = ST_OK, stall = 0;
+    double best_rel = bnorm > 0.0 ? gamma / bnorm : 0.0;
     if (bnorm == 0.0) {
       for (int gi = g0 + tid; gi < g1; gi += NTB)
         for (int u = 0; u < VEC; ++u)
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(Batc
         const double rel = gamma / bnorm;
         if (!isfinite(rel)) { status = ST_NONFINITE; break; }
         if (rel <= a.rtol) { status = ST_OK; break; }
-        if (its >= a.max_iters) { status = ST_NOT_CONVERGED; break; }
+        if (its >= a.max_iters || stall >= IR_STALL_LIMIT) { status = ST_NOT_CONVERGED; break; }
         // ---- one inner GMRES(m) cycle on A u = r, v_0 = r / gamma ----
         double sigma = 1.0 / gamma;
         if (tid == 0) g[0] = 1.0;
@@ -420,6 +421,12 @@ __global__ void __launch_bounds__(NTB, sizeof(W) == 4 ? 2 : 1) k_batched_ir(Batc
         ++outer;
         residual();
         gamma = sqrt(sums[0]);
+        if (gamma / bnorm < best_rel * (1.0 - 1e-3)) {  // the stall test of the single solver
+          best_rel = gamma / bnorm;
+          stall = 0;
+        } else {
+          ++stall;
+        }
       }
     }
     if (rank == 0 && tid == 0) {

@@ -141,8 +141,14 @@ struct DevState {
   double sigma;      // 1 / norm of the next SpMV source vector
   double wnorm;      // ||A v_j|| of the current step (breakdown test)
   double u_work;     // unit roundoff of the working precision
+  double best_rel;   // IR: smallest explicit relative residual so far
+  int stall;         // IR: refinement steps since best_rel last dropped by 0.1%
   unsigned int ticket[4];
 };
+
+// GMRES-IR stops as NOT_CONVERGED after this many refinement steps without progress (an
+// inner precision too coarse for the problem makes the iteration stall or diverge).
+constexpr int IR_STALL_LIMIT = 20;
 
 // Small dense arrays of the cycle (FP64, device memory, one allocation).
 struct Arrays {

@@ -1091,12 +1091,23 @@ __global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, con
       const double bnorm = st->bnorm;
       st->gamma = gamma;
       st->relres = bnorm > 0.0 ? gamma / bnorm : 0.0;
+      // GMRES-IR: progress of the refinement (explicit residual), for the stall test
+      if (st->mode == 1) {
+        const double rel = st->relres;
+        if (first || rel < st->best_rel * (1.0 - 1e-3)) {
+          st->best_rel = rel;
+          st->stall = 0;
+        } else {
+          st->stall += 1;
+        }
+      }
       int stop = 1, status = ST_OK;
       if (!isfinite(gamma) || !isfinite(bnorm)) status = ST_NONFINITE;
       else if (bnorm == 0.0) { st->zero_rhs = 1; st->relres = 0.0; }
       else if (gamma <= st->rtol * bnorm) status = ST_OK;
       else if (st->singular) status = ST_BREAKDOWN;
       else if (st->iters >= st->max_iters) status = ST_NOT_CONVERGED;
+      else if (st->mode == 1 && st->stall >= IR_STALL_LIMIT) status = ST_NOT_CONVERGED;
       else stop = 0;
       st->status = status;
       if (!stop) {

@@ -251,3 +251,22 @@ def test_full_size_3d_ir_and_fp64(g, torch, cube):
     assert out["ir"][0].iters <= out["gmres"][0].iters + 150
     xi, xg = out["ir"][1], out["gmres"][1]
     assert np.linalg.norm(xi - xg) / np.linalg.norm(xg) <= 1e-6
+
+
+def test_ir_gives_up_on_stalled_refinement():
+    """The stall rule of the oracle (no 0.1% progress in IR_STALL_LIMIT refinement steps):
+    GMRES(1) cannot reduce the residual of a 90-degree rotation."""
+    import paper_2109_01232_b300 as g
+    import torch
+    from oracle.gmres import IR_STALL_LIMIT
+    A = gen.Problem("rot", 2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32),
+                    np.array([1.0, -1.0]))
+    b = torch.tensor([1.0, 0.0], device="cuda", dtype=torch.float64)
+    x = torch.zeros(2, device="cuda", dtype=torch.float64)
+    r = g.gmres_ir_solve(g.DeviceCSR.from_problem(A), b, x, restart_m=1, rtol=1e-10)
+    assert r.status == g.NOT_CONVERGED and r.outer == IR_STALL_LIMIT and r.iters == IR_STALL_LIMIT
+    batch = g.DeviceBatch([A, A])
+    bb = torch.tensor([1.0, 0.0, 0.0, 2.0], device="cuda", dtype=torch.float64)
+    xb = torch.zeros_like(bb)
+    res = g.BatchPlan(batch, autotune=False, restart_m=1).solve(bb, xb)
+    assert list(res.status) == [g.NOT_CONVERGED] * 2 and list(res.outer) == [IR_STALL_LIMIT] * 2

@@ -13,7 +13,7 @@ import pytest
 
 import gen
 import oracle
-from oracle.gmres import _fp64
+from oracle.gmres import IR_STALL_LIMIT, _fp64
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -315,3 +315,14 @@ def test_fd_switch_at_zero_is_plain_fp64_gmres_and_converges_late():
     assert i32.iters == 0 and i64.iters == info.iters
     x1, i32b, i64b = oracle.gmres_fd(p, b, switch_iter=100, m=20)
     assert i32b.iters == 100 and i64b.relres <= 1e-10
+
+
+def test_ir_stops_after_stalled_refinement():
+    """GMRES(1) makes no progress on a 90-degree rotation (A r is orthogonal to r), so the
+    refinement stalls and gives up after IR_STALL_LIMIT steps without 0.1% progress."""
+    A = gen.Problem("rot", 2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32),
+                    np.array([1.0, -1.0]))
+    x, info = oracle.gmres_ir(A, np.array([1.0, 0.0]), m=1, rtol=1e-10)
+    assert info.status == oracle.NOT_CONVERGED
+    assert info.outer == IR_STALL_LIMIT and info.iters == info.outer
+    assert info.relres == 1.0 and np.all(x == 0.0)
