@@ -243,6 +243,19 @@ def run_batched(g, torch, peak):
                     "frac": nbytes / t / 1e9 / peak}}
 
 
+# ------------------------------------------------------------- multi-rank ----
+def max_over_ranks(value: float, dist=None) -> float:
+    """The largest `value` over the ranks of the default process group (replicas: every
+    rank times the same workload, the job is as slow as its slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------- our arm ----
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -290,11 +303,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     if dist:
         dist.barrier()
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), dist)
     per_solve_s = elapsed_ms / 1e3 / (args.steps * len(insts))
     for rs in results:
         for r in rs:
