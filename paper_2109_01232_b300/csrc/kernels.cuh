@@ -266,6 +266,33 @@ __device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long l
   }
 }
 
+// dots_to_acc over V[0..nc) with the columns taken in descending order (the same value
+// per column).  k_cgs_u1 calls it right after update_all has loaded the same columns in
+// ascending order, so the newest lines, the likeliest to still be in L1, are read first.
+template <class S, class W, int VEC>
+__device__ __forceinline__ void dots_to_acc_desc(const S* __restrict__ V, long long ld,
+                                                 long long base, int nc, const W (&wv)[VEC],
+                                                 W* acc) {
+  const int lane = threadIdx.x & 31;
+  int c = nc;
+  for (; c > (nc & ~7); --c) {
+    W d[1];
+    dot_cols<1, false>(V, ld, base, c - 1, wv, d);
+    const W t = warp_sum(d[0]);
+    if (lane == 0) acc[c - 1] += t;
+  }
+  for (; c >= 8; c -= 8) {
+    W d[8];
+    dot_cols<8, false>(V, ld, base, c - 8, wv, d);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) d[b] = warp_sum(d[b]);
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[c - 8 + b] += d[b];
+    }
+  }
+}
+
 // w -= V[0..nc) coef for this thread's rows.  EF: see update_cols.
 template <bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void update_all(const S* __restrict__ V, long long ld, long long base,
@@ -819,7 +846,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_cgs_u1(con
     ldv(win + base, wv);
     update_all<false, S, W, VEC>(V, ld, base, nc, coef, wv);
     stv(wout + base, wv);
-    dots_to_acc<false, S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
+    dots_to_acc_desc<S, W, VEC>(V, ld, base, nc, wv, acc + warp * nc);
   }
   __syncthreads();
   write_cta_partials(acc, nc, nc, parts.p2);
