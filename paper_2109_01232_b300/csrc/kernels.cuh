@@ -581,8 +581,12 @@ __device__ __forceinline__ GivensRot givens_rotation(double x, double hn2, doubl
   return g;
 }
 
-// Shared-memory doubles that finalize_step needs (for js < LSQ_MAX).
-constexpr int GIVENS_SH = 4 * (LSQ_MAX + 2);
+// Shared-memory doubles that finalize_step needs (for js < LSQ_MAX): the column, the old
+// rotations and the rotated column (at most 4 LSQ_MAX), then GIVENS_SCAL scalars of the
+// solver state at offset GIVENS_SCAL_AT.
+constexpr int GIVENS_SCAL_AT = 4 * (LSQ_MAX + 2);
+constexpr int GIVENS_SCAL = 6;
+constexpr int GIVENS_SH = GIVENS_SCAL_AT + 8;
 
 // Givens update of step js (Algorithm 1's least squares solved incrementally, FP64) with
 // the stop decision.  Called by every thread of the CTA; `sh` holds GIVENS_SH doubles of
@@ -598,30 +602,51 @@ constexpr int GIVENS_SH = 4 * (LSQ_MAX + 2);
 // 4 js of them costs about 0.2 us per rotation, so warp 0 evaluates it as a scan: each lane
 // composes the affine maps of a segment of rotations, a shuffle scan gives every lane the
 // x entering its segment, and the lanes replay their segments in parallel.
-__device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2, double wn2,
-                              bool writer, double* sh, int* done_out, double* sigma_out) {
+//
+// The update is split so that a kernel can issue its global loads early:
+// finalize_load (no barrier) gathers the column, the old rotations and the state scalars
+// into `sh`; finalize_compute, after a CTA barrier, does the rest.  finalize_step is the
+// two with the barrier between them.
+__device__ __forceinline__ void finalize_load(const DevState* st, const Arrays& a, int js,
+                                              double* sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* col = sh;                 // js + 2: the new column h (H[:, js] before rotation)
   double* cs = sh + (js + 2);       // js
   double* sn = cs + (js + 1);       // js
-  double* rot = sn + (js + 1);      // js: R[0..js, js]
-  const int ldh = st->m + 1;
   if (warp == 2) {
-    double* Hc = a.H + (long long)js * ldh;
-    for (int i = lane; i <= js; i += 32) {
-      const double h = a.h1[i] + a.h2[i];
-      col[i] = h;
-      if (writer) Hc[i] = h;
-    }
+    for (int i = lane; i <= js; i += 32) col[i] = a.h1[i] + a.h2[i];
   } else if (warp == 3) {
     for (int i = lane; i < js; i += 32) {
       cs[i] = a.cs[i];
       sn[i] = a.sn[i];
     }
+  } else if (warp == 1 && lane == 0) {
+    double* sc = sh + GIVENS_SCAL_AT;
+    sc[0] = a.gabs[js];
+    sc[1] = st->u_work;
+    sc[2] = st->stop_rel;
+    sc[3] = (double)(st->iters0 + js + 1);  // exact: step counts stay far below 2^53
+    sc[4] = (double)st->max_iters;          // compared as doubles with sc[3]
+    sc[5] = (double)st->m;
   }
-  __syncthreads();
+}
+
+__device__ void finalize_compute(DevState* st, const Arrays& a, int js, double hn2, double wn2,
+                                 bool writer, double* sh, int* done_out, double* sigma_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* col = sh;
+  const double* cs = sh + (js + 2);
+  const double* sn = cs + (js + 1);
+  double* rot = sh + (3 * js + 4);  // js: R[0..js, js]
+  const double* sc = sh + GIVENS_SCAL_AT;
+  const int m = (int)sc[5];
+  const int ldh = m + 1;
   __shared__ int s_done;
   __shared__ double s_sigma;
+  if (writer && warp == 2) {
+    double* Hc = a.H + (long long)js * ldh;
+    for (int i = lane; i <= js; i += 32) Hc[i] = col[i];
+  }
   if (warp == 0) {
     const double x = givens_scan(js, col, cs, sn, rot);
     const GivensRot gr = givens_rotation(x, hn2, wn2);
@@ -632,11 +657,11 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2,
     }
     if (lane == 0) {
       const double hn = gr.hn, wnorm = gr.wnorm, c = gr.c, s = gr.s, rjj = gr.rjj;
-      const double res = a.gabs[js] * fabs(s);
-      const long long iters = st->iters0 + js + 1;
+      const double res = sc[0] * fabs(s);
+      const long long iters = (long long)sc[3];
       const bool bad = !isfinite(hn) || !isfinite(res) || !isfinite(rjj);
-      const int brk = hn <= 16.0 * st->u_work * wnorm;
-      const int done = bad || brk || res <= st->stop_rel || js + 1 >= st->m || iters >= st->max_iters;
+      const int brk = hn <= 16.0 * sc[1] * wnorm;
+      const int done = bad || brk || res <= sc[2] || js + 1 >= m || sc[3] >= sc[4];
       s_done = done;
       s_sigma = brk ? 0.0 : gr.inv_hn;
       if (writer) {
@@ -665,6 +690,13 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2,
   __syncthreads();
   *done_out = s_done;
   *sigma_out = s_sigma;
+}
+
+__device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2, double wn2,
+                              bool writer, double* sh, int* done_out, double* sigma_out) {
+  finalize_load(st, a, js, sh);
+  __syncthreads();
+  finalize_compute(st, a, js, hn2, wn2, writer, sh, done_out, sigma_out);
 }
 
 template <int P>
@@ -700,6 +732,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
   W* acc = ws + WT;
   __shared__ int s_skip;
   __shared__ W s_mine[2], s_nrm[2];
+  // the Givens update's global loads go out before the prologue's barriers
+  if (!PLAIN && j > 0) finalize_load(st, arr, j - 1, gsh);
   if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
   __syncthreads();
   double sigma = 1.0;
@@ -711,8 +745,8 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     };
     if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, &s_skip)) return;
     int done;
-    finalize_step(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh, &done,
-                  &sigma);
+    finalize_compute(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh,
+                     &done, &sigma);
     if (done) return;
   } else {
     if (s_skip) return;
