@@ -482,27 +482,31 @@ struct ColumnSrc {    // column c of the partials: `count` values at `ptr`
   int count;
 };
 
-// col(c) -> ColumnSrc<W>.  mine and out hold ncol values (shared memory); *s_skip is this
-// CTA's skip flag (shared memory, set before the call).  Returns false when the cluster
-// skips; then out is not written.  Called by all threads of every CTA of the cluster.
-template <class W, class ColF>
+// col(c) -> ColumnSrc<W>.  mine and out hold ncol values (shared memory).  skip_flag()
+// is this CTA's skip flag, evaluated by thread 0 (its loads are in flight together with
+// the partial sums' loads, which are made whether or not the CTA skips: their buffers
+// always exist, and a skipping cluster discards the sums).  Returns false when the
+// cluster skips; then out is not written.  Called by all threads of every CTA of the
+// cluster.
+template <class W, class ColF, class SkipF>
 __device__ __forceinline__ bool cluster_column_sums(const ColF& col, int ncol, W* mine, W* out,
-                                                    const int* s_skip) {
+                                                    const SkipF& skip_flag) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int s_any;
-  if (!*s_skip) {
-    for (int c = rank + CL * warp; c < ncol; c += CL * NWARP) {
-      const ColumnSrc<W> src = col(c);
-      const W v = warp_sum_partials(src.ptr, src.count);
-      if (lane == 0) mine[c] = v;
-    }
+  __shared__ int s_flag, s_any;
+  int flag = 0;
+  if (threadIdx.x == 0) flag = skip_flag();
+  for (int c = rank + CL * warp; c < ncol; c += CL * NWARP) {
+    const ColumnSrc<W> src = col(c);
+    const W v = warp_sum_partials(src.ptr, src.count);
+    if (lane == 0) mine[c] = v;
   }
+  if (threadIdx.x == 0) s_flag = flag;
   cl.sync();
   if (warp == 0) {
-    int f = lane < CL ? *cl.map_shared_rank(s_skip, lane) : 0;
+    int f = lane < CL ? *cl.map_shared_rank(&s_flag, lane) : 0;
     f = __any_sync(0xffffffffu, f);
     if (lane == 0) s_any = f;
   }
@@ -734,8 +738,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
   __shared__ W s_mine[2], s_nrm[2];
   // the Givens update's global loads go out before the prologue's barriers
   if (!PLAIN && j > 0) finalize_load(st, arr, j - 1, gsh);
-  if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
-  __syncthreads();
+  const auto skip_flag = [&] { return read_flag(&st->stop) | read_flag(&st->cycle_done); };
   double sigma = 1.0;
   if (!PLAIN && j > 0) {  // with a polynomial, k_poly_start applied the update
     // ||w''|| of step j-1 (k_cgs_u2's partials) and ||A v_{j-1}|| (norm column of step j-1)
@@ -743,12 +746,14 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     const auto col = [&](int c) {
       return c == 0 ? ColumnSrc<W>{parts.p3, parts.g2} : ColumnSrc<W>{pn, parts.g1};
     };
-    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, &s_skip)) return;
+    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, skip_flag)) return;
     int done;
     finalize_compute(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh,
                      &done, &sigma);
     if (done) return;
   } else {
+    if (tid == 0) s_skip = skip_flag();
+    __syncthreads();
     if (s_skip) return;
     if (!PLAIN) sigma = st->sigma;
   }
@@ -859,15 +864,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_cgs_u1(con
   const int nc = j + 1;
   W* coef = reinterpret_cast<W*>(smem_raw);
   W* acc = coef + nc;
-  __shared__ int s_skip;
   __shared__ W s_mine[LSQ_MAX + 2];
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
-  __syncthreads();
   const W* pj = parts.p1_of(j);
   const int gp = parts.g1;
   const auto col = [&](int c) { return ColumnSrc<W>{pj + (long long)c * gp, gp}; };
-  if (!cluster_column_sums<W>(col, nc, s_mine, coef, &s_skip)) return;
+  const auto skip_flag = [&] { return read_flag(&st->stop) | read_flag(&st->cycle_done); };
+  if (!cluster_column_sums<W>(col, nc, s_mine, coef, skip_flag)) return;
   for (int i = tid; i < NWARP * nc; i += NT) acc[i] = W(0);
   coefs_from_sums(coef, nc, v_scale, h1);
   const long long ngroups = ld / VEC;
@@ -903,15 +906,13 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_cgs_u2(con
   const int nc = j + 1;
   W* coef = reinterpret_cast<W*>(smem_raw);
   __shared__ W accw[NWARP];
-  __shared__ int s_skip;
   __shared__ W s_mine[LSQ_MAX + 2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_skip = read_flag(&st->stop) | read_flag(&st->cycle_done);
-  __syncthreads();
   const W* pj = parts.p2;
   const int gp = parts.g2;
   const auto col = [&](int c) { return ColumnSrc<W>{pj + (long long)c * gp, gp}; };
-  if (!cluster_column_sums<W>(col, nc, s_mine, coef, &s_skip)) return;
+  const auto skip_flag = [&] { return read_flag(&st->stop) | read_flag(&st->cycle_done); };
+  if (!cluster_column_sums<W>(col, nc, s_mine, coef, skip_flag)) return;
   coefs_from_sums(coef, nc, v_scale, h2);
   W nrm = W(0);
   const long long ngroups = ld / VEC;

@@ -40,20 +40,21 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(co
   __shared__ double gsh[GIVENS_SH];
   __shared__ int s_skip;
   __shared__ W s_mine[2], s_nrm[2];
-  if (threadIdx.x == 0) s_skip = poly_skip(st, 1);
-  __syncthreads();
   double sigma;
   if (j > 0) {
+    finalize_load(st, arr, j - 1, gsh);
     const W* pn = parts.p1_of(j - 1) + (long long)j * parts.g1;
     const auto col = [&](int c) {
       return c == 0 ? ColumnSrc<W>{parts.p3, parts.g2} : ColumnSrc<W>{pn, parts.g1};
     };
-    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, &s_skip)) return;
+    if (!cluster_column_sums<W>(col, 2, s_mine, s_nrm, [&] { return poly_skip(st, 1); })) return;
     int done;
-    finalize_step(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh, &done,
-                  &sigma);
+    finalize_compute(st, arr, j - 1, (double)s_nrm[0], (double)s_nrm[1], blockIdx.x == 0, gsh,
+                     &done, &sigma);
     if (done) return;
   } else {
+    if (threadIdx.x == 0) s_skip = poly_skip(st, 1);
+    __syncthreads();
     if (s_skip) return;
     sigma = st->sigma;
   }
