@@ -22,3 +22,4 @@ from .poly import (  # noqa: F401
     splitmix64_raw, splitmix64_uniform, harmonic_ritz, leja_order, poly_roots, poly_apply,
 )
 from . import selector  # noqa: F401
+from . import precond  # noqa: F401

@@ -21,7 +21,8 @@ Strategies for GMRES on GPUs", arXiv 2109.01232):
 * Section 3.3, GMRES-FD: FP32 GMRES(m) up to a restart, then FP64 GMRES(m)
   continuing from that x.
 * Section 3.4: right preconditioning A M^{-1} (M x) = b with M^{-1} = p(A)
-  (see oracle/poly.py).
+  (see oracle/poly.py), or any M^{-1} given as a function (`right_prec`: block
+  Jacobi, see oracle/precond.py), whose result is rounded to the working precision.
 
 Readings where the paper is silent (each is listed in the design doc):
 * Convergence is measured by the explicit ||b - A x||_2 / ||b||_2 (Section
@@ -254,7 +255,7 @@ def _check_inputs(A, b):
 
 
 def gmres(A, b, x0=None, m: int = 50, rtol: float = 1e-10, max_iters: int = 100000,
-          poly_roots=None, precision: str = "fp64") -> tuple[np.ndarray, Info]:
+          poly_roots=None, precision: str = "fp64", right_prec=None) -> tuple[np.ndarray, Info]:
     """Restarted GMRES(m) (Algorithm 1, CGS2, right polynomial preconditioner optional).
 
     precision='fp64' is the plain double-precision solver.  precision='fp32' runs the whole
@@ -288,6 +289,9 @@ def gmres(A, b, x0=None, m: int = 50, rtol: float = 1e-10, max_iters: int = 1000
 
         def op(v):
             return opA(poly_apply(opA, poly_roots, v, rw))
+    elif right_prec is not None:
+        def op(v):
+            return opA(rw(right_prec(v)))
 
     r = rw(b - opA(x))
     gamma = float(np.linalg.norm(r))
@@ -309,6 +313,8 @@ def gmres(A, b, x0=None, m: int = 50, rtol: float = 1e-10, max_iters: int = 1000
         if poly_roots is not None and len(poly_roots):
             from .poly import poly_apply
             u = poly_apply(opA, poly_roots, u, rw)
+        elif right_prec is not None:
+            u = rw(right_prec(u))
         x = rw(x + gamma * u)
         r = rw(b - opA(x))
         gamma = float(np.linalg.norm(r))
@@ -329,7 +335,7 @@ IR_STALL_LIMIT = 20
 
 def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32",
              inner_rtol: float = 0.0, max_iters: int = 100000, poly_roots=None,
-             arith: str = "fp32") -> tuple[np.ndarray, Info]:
+             arith: str = "fp32", right_prec=None) -> tuple[np.ndarray, Info]:
     """GMRES-IR (Algorithm 2): FP64 residual and update around a low-precision GMRES(m)
     cycle.  `inner` is the storage precision of A's copy and of the basis (fp32, fp16, bf16;
     fp64 reproduces plain restarted GMRES with an explicit residual test at each restart)."""
@@ -353,6 +359,9 @@ def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32
 
         def op(v):
             return op_low(poly_apply(op_low, poly_roots, v, prec.rw))
+    elif right_prec is not None:
+        def op(v):
+            return op_low(prec.rw(right_prec(v)))
 
     r = b - spmv(A, x)  # [double]
     gamma = float(np.linalg.norm(r))
@@ -375,6 +384,8 @@ def gmres_ir(A, b, x0=None, m: int = 50, rtol: float = 1e-10, inner: str = "fp32
         if poly_roots is not None and len(poly_roots):
             from .poly import poly_apply
             u = poly_apply(op_low, poly_roots, u, prec.rw)
+        elif right_prec is not None:
+            u = prec.rw(right_prec(u))
         x = x + gamma * u  # [double]
         r = b - spmv(A, x)  # [double]
         gamma = float(np.linalg.norm(r))
