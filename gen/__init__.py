@@ -26,4 +26,8 @@ from .stencil import (  # noqa: F401
     laplace_3d,
     box_2d,
     star_3d,
+    box_3d,
+    shuffled,
+    scaled,
+    config_bj,
 )

@@ -292,3 +292,49 @@ def star_3d(side: int) -> Problem:
     offs = [tuple(s * r if k == a else 0 for k in range(3)) for a in range(3) for s in (1, -1)
             for r in (1, 2)]
     return stencil_matrix((side, side, side), offs, f"star3d_{side}")
+
+
+def box_3d(side: int) -> Problem:
+    """27-point box stencil in 3D (SPD; a stand-in for 3D finite-element matrices with about
+    27 entries per row)."""
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+            if (dx, dy, dz) != (0, 0, 0)]
+    return stencil_matrix((side, side, side), offs, f"box3d_{side}")
+
+
+def shuffled(p: Problem, seed: int) -> Problem:
+    """The same matrix with its unknowns relabelled by a seeded random permutation q
+    (row/column i of the result is row/column q[i] of p): an arbitrary numbering like a
+    matrix collection's, for the reordering to undo."""
+    q = _rng(seed).permutation(p.n)
+    A = sp.csr_matrix((p.vals, p.col_idx, p.row_ptr), shape=(p.n, p.n))[q][:, q].tocsr()
+    A.sort_indices()
+    meta = dict(p.meta, shuffle_seed=int(seed))
+    return Problem(p.name + f"_shuf{seed}", p.n, A.indptr.astype(np.int32),
+                   A.indices.astype(np.int32), A.data.astype(np.float64), meta)
+
+
+def scaled(p: Problem, sigma: float, seed: int) -> Problem:
+    """S A S with S = diag(exp(sigma z)), z ~ N(0, 1) seeded: the badly scaled unknowns of
+    assembled engineering matrices (an SPD A stays SPD), which Jacobi-type preconditioners
+    undo."""
+    d = np.exp(sigma * _rng(seed).standard_normal(p.n))
+    A = sp.csr_matrix((p.vals, p.col_idx, p.row_ptr), shape=(p.n, p.n))
+    A = (sp.diags(d) @ A @ sp.diags(d)).tocsr()
+    A.sort_indices()
+    meta = dict(p.meta, scale_sigma=float(sigma), scale_seed=int(seed))
+    return Problem(p.name + f"_scaled{sigma:g}", p.n, A.indptr.astype(np.int32),
+                   A.indices.astype(np.int32), A.data.astype(np.float64), meta)
+
+
+def config_bj() -> list[tuple[Problem, int]]:
+    """The block-Jacobi workloads (Section 5.8's "J k" rows, whose SuiteSparse matrices are
+    absent): synthetic stand-ins, badly scaled (sigma = 1) and in a shuffled numbering,
+    each with its block size.
+      * SPD 3D, 27-point box stencil on 60^3 (n = 216,000, ~27 entries per row), k = 42
+        (for the SPD finite-element row, "J 42");
+      * nonsymmetric 3D upwind convection-diffusion, 48^3 (n = 110,592, 7 per row), Pe 50,
+        k = 1 (for the nonsymmetric row, "J 1")."""
+    return [(shuffled(scaled(box_3d(60), 1.0, 13), 11), 42),
+            (shuffled(scaled(conv_diff_3d(48, 50.0, (0.6, 0.8, 0.0)), 1.0, 14), 12), 1)]
+

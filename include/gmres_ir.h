@@ -86,6 +86,15 @@ typedef struct {
                                copy of A, FP32 vectors, cast in and out) under an FP64 cycle --
                                the paper's FP64 GMRES with an FP32 polynomial (Section 5.4);
                                ignored when the cycle is not FP64 */
+  int32_t bj_block;         /* block size k of the block-Jacobi right preconditioner
+                               (Section 5.8, "J k"), 1..GMRES_MAX_BJ_BLOCK; 0 = none.  The
+                               diagonal blocks [q k, min((q+1) k, n)) are LU-factored with
+                               partial pivoting in FP64 at plan creation and applied in the
+                               cycle's working precision (FP64 for FP64 plans, FP32
+                               otherwise).  Not combined with poly_degree > 0. */
+  int32_t bj_rcm;           /* nonzero: reorder the system with reverse Cuthill-McKee at
+                               plan creation (Section 5.8; before the blocks are taken);
+                               b, x0 and x stay in the caller's numbering */
 } gmres_params;
 
 /* Forms of the two CGS2 update kernels (the same arithmetic per row; both produce the
@@ -100,6 +109,7 @@ typedef enum {
 
 #define GMRES_MAX_RESTART 512
 #define GMRES_MAX_POLY_DEGREE 96
+#define GMRES_MAX_BJ_BLOCK 64
 
 /* Solve statistics (written by every solve entry point when non-NULL). */
 typedef struct {
@@ -206,6 +216,30 @@ int gmres_poly_roots(const gmres_csr* A, int32_t degree, uint64_t seed, const do
  * y: DEVICE, n values of the polynomial's working type (double for FP64 plans,
  * float otherwise and for FP64 plans created with poly_in_fp32). */
 int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream);
+
+/* y = M^{-1} v with the plan's block-Jacobi factors (Section 5.8; the plan must have
+ * bj_block > 0): per block, the pivoted forward and back substitutions in the working
+ * precision.  v: DEVICE, n doubles; y: DEVICE, n values of the working type (double for
+ * FP64 plans, float otherwise).  Both in the plan's numbering (reordered when bj_rcm).
+ * Asynchronous on `stream` (y is ready in stream order).  GMRES_ERR_INVALID without
+ * block Jacobi or with a NULL pointer. */
+int gmres_plan_bj_apply(gmres_plan plan, const double* v, void* y, void* stream);
+
+/* The plan's reverse Cuthill-McKee permutation: *reordered = 1 and, if perm is not NULL,
+ * perm[new] = old (HOST, n entries) when the plan was created with bj_rcm; *reordered = 0
+ * otherwise (perm untouched).  The plan's test entry points (spmv, arnoldi, bj_apply,
+ * poly_apply) work in the reordered numbering; solves take and return the caller's. */
+int gmres_plan_perm(gmres_plan plan, int32_t* perm, int32_t* reordered);
+
+/* Reverse Cuthill-McKee ordering of a CSR structure (Section 5.8), on the host: all
+ * arrays HOST; perm[new] = old, n entries, written by the call.  The graph is the
+ * structure of A + A^T without the diagonal; vertices rank by (degree, index); each
+ * connected component (in the order of its lowest-ranked vertex) starts from the
+ * pseudo-peripheral vertex of the George-Liu iteration and is ordered by a breadth-first
+ * search that takes unvisited neighbours in rank order; the whole order is reversed.
+ * GMRES_ERR_INVALID for a malformed structure (row_ptr[0] != 0, decreasing row_ptr,
+ * column out of range) or a NULL pointer with n > 0. */
+int gmres_rcm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* perm);
 
 /* The plan's polynomial roots (HOST arrays of at least poly_degree+1 entries,
  * either may be NULL) in the order they are applied; *nroots = 0 without a

@@ -25,6 +25,7 @@ STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: "ERR_I
  ERR_DEVICE_TIMEOUT) = range(9)
 STATUS_SOLVER = (NOT_CONVERGED, BREAKDOWN, NONFINITE)  # outcomes of a solve, not errors
 MAX_RESTART = 512
+MAX_BJ_BLOCK = 64
 MAX_POLY_DEGREE = 96
 
 
@@ -44,7 +45,8 @@ class params_t(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("inner_prec", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32),
-                ("cgs_kernel", ctypes.c_int32), ("poly_in_fp32", ctypes.c_int32)]
+                ("cgs_kernel", ctypes.c_int32), ("poly_in_fp32", ctypes.c_int32),
+                ("bj_block", ctypes.c_int32), ("bj_rcm", ctypes.c_int32)]
 
 
 class stats_t(ctypes.Structure):
@@ -100,6 +102,9 @@ _SIGNATURES = {
     "gmres_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
+    "gmres_plan_bj_apply": (ctypes.c_int, [_P, _P, _P, _P]),
+    "gmres_plan_perm": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32)]),
+    "gmres_rcm": (ctypes.c_int, [_I32, _P, _P, _P]),
     "gmres_spmv_fp64_noalloc": (ctypes.c_int, [ctypes.POINTER(csr_t), _P, _P, _P]),
     "gmres_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(csr_batch_t),
                                                ctypes.POINTER(params_t), _I32, _P]),
@@ -353,6 +358,22 @@ class Plan:
                "poly_apply")
         return y
 
+    def bj_apply(self, v, stream=None):
+        """y = M^{-1} v with the plan's block-Jacobi factors (working dtype; the plan's
+        numbering, i.e. reordered when the plan was created with bj_rcm)."""
+        torch = _torch()
+        y = torch.empty(self.A.n, dtype=self.work_dtype, device="cuda")
+        _check(lib().gmres_plan_bj_apply(self.handle, _ptr(v), _ptr(y), _stream(stream)),
+               "bj_apply")
+        return y
+
+    def perm(self) -> np.ndarray | None:
+        """perm[new] = old of the plan's reverse Cuthill-McKee reordering, or None."""
+        out = np.zeros(max(self.A.n, 1), dtype=np.int32)
+        flag = ctypes.c_int32(0)
+        _check(lib().gmres_plan_perm(self.handle, out.ctypes.data, ctypes.byref(flag)), "perm")
+        return out[:self.A.n] if flag.value else None
+
     def roots(self) -> np.ndarray:
         n = ctypes.c_int32(0)
         _check(lib().gmres_plan_poly_roots(self.handle, None, None, ctypes.byref(n)), "roots")
@@ -399,6 +420,17 @@ def poly_roots(A: DeviceCSR, degree: int, seed: int = 0, v0=None, stream=None) -
                                   re.ctypes.data, im.ctypes.data, ctypes.byref(nr),
                                   _stream(stream)), "poly_roots")
     return re[:nr.value] + 1j * im[:nr.value]
+
+
+def rcm(row_ptr, col_idx, n: int | None = None) -> np.ndarray:
+    """Reverse Cuthill-McKee permutation (perm[new] = old) of a CSR structure, computed by
+    the library on the host (no GPU needed)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    n = int(rp.size - 1 if n is None else n)
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().gmres_rcm(n, rp.ctypes.data, ci.ctypes.data, perm.ctypes.data), "rcm")
+    return perm[:n]
 
 
 def splitmix64(n: int, seed: int, stream=None):

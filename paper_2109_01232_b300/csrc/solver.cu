@@ -21,6 +21,8 @@
 #include "cgs_tma.cuh"
 #include "poly_kernels.cuh"
 #include "poly_host.h"
+#include "bj_kernels.cuh"
+#include "rcm_host.h"
 
 namespace gm {
 
@@ -89,6 +91,15 @@ struct Plan {
   void *pa = nullptr, *pb = nullptr, *pt = nullptr, *py = nullptr;  // working-type vectors
   bool poly32 = false;           // FP64 cycle, polynomial applied in FP32
   void* sell_vals32 = nullptr;   // FP32 values of the SELL copy (poly32)
+  // block-Jacobi preconditioner (right) and the reverse Cuthill-McKee reordering
+  int bj = 0;                    // block size k; 0 = none
+  void* bj_lu = nullptr;         // factors of the diagonal blocks (working type, k*k per block)
+  int* bj_rowp = nullptr;        // pivot order of each block's rows
+  int grid_bj = 1;
+  int* perm = nullptr;           // perm[new] = old (device); null without reordering
+  int32_t* pA_rp = nullptr;      // the plan's reordered copy of A (device CSR)
+  int32_t* pA_ci = nullptr;
+  double* pA_v = nullptr;
   int grid_elem = 1;
   double t_setup_ms = 0.0;
 };
@@ -177,6 +188,12 @@ static void launch_poly(Plan& pl, int in_cycle, cudaStream_t s) {
   }
 }
 
+// Dynamic shared memory of k_bj_apply for the plan's block size.
+template <class W>
+static size_t bj_smem(const Plan& pl) {
+  return sizeof(W) * (size_t)BJ_APPLY_WARPS * bj_slot(pl.bj);
+}
+
 // Kernel `which` (0: fused SpMV + first-pass dots -- with a polynomial preconditioner the
 // whole w = A p(A) v_j chain --, 1: first CGS update + second-pass dots, 2: second CGS
 // update + norm + Givens) of Arnoldi step j.
@@ -191,6 +208,20 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
   const StepParts<W> sp = step_parts<P>(pl);
   if (which == 0) {
     const size_t sm1 = SellSmem<P>::bytes(j + 2);
+    if (pl.bj) {  // w = A M^{-1} v_j: store v_j, z = M^{-1} v_j, SpMV of z
+      if (j == 0)
+        k_poly_start<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
+                                                           (W*)pl.pa, sp, pl.st, pl.arr);
+      else
+        k_poly_start<P, W><<<pl.grid_elem, NT, 0, s>>>(w3, pl.v_scale, pl.n, V, pl.ld, j,
+                                                      (W*)pl.pa, sp, pl.st, pl.arr);
+      k_bj_apply<W><<<pl.grid_bj, 32 * BJ_APPLY_WARPS, bj_smem<W>(pl), s>>>((const W*)pl.bj_lu, pl.bj_rowp, pl.n, pl.bj,
+                                               (const W*)pl.pa, (W*)pl.py, pl.st, 1);
+      k_spmv_sell<P, W, true><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, pl.a_scale,
+          (const W*)pl.py, pl.v_scale, V, j, w1, sp, pl.st, pl.arr);
+      return;
+    }
     if (!pl.poly.empty() && pl.poly32) {  // FP64 cycle, polynomial in FP32
       if (j == 0)
         k_poly_start<P, double, float><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
@@ -277,7 +308,13 @@ static void launch_tail_kernel(Plan& pl, int which, cudaStream_t s) {
     k_lsq<<<1, NT, packed ? sizeof(double) * (size_t)pl.m * (pl.m + 1) / 2 : 0, s>>>(pl.st, pl.arr,
                                                                                    packed);
   } else if (which == 1) {
-    if (!pl.poly.empty()) {
+    if (pl.bj) {  // x += gamma M^{-1} (V y)
+      k_vy<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>((const S*)pl.V, pl.ld, pl.v_scale,
+                                                               pl.st, pl.arr.y, (W*)pl.pa);
+      k_bj_apply<W><<<pl.grid_bj, 32 * BJ_APPLY_WARPS, bj_smem<W>(pl), s>>>((const W*)pl.bj_lu, pl.bj_rowp, pl.n, pl.bj,
+                                               (const W*)pl.pa, (W*)pl.py, pl.st, 0);
+      k_xadd<W><<<pl.grid_elem, NT, 0, s>>>((const W*)pl.py, pl.xb, pl.n, pl.st);
+    } else if (!pl.poly.empty()) {
       if (pl.poly32) {
         k_vy<P, float><<<pl.grid_vec, NT, sizeof(W) * (size_t)pl.m, s>>>(
             (const S*)pl.V, pl.ld, pl.v_scale, pl.st, pl.arr.y, (float*)pl.pa);
@@ -412,6 +449,12 @@ static void plan_free(Plan* pl) {
   cudaFree(pl->pb);
   cudaFree(pl->pt);
   cudaFree(pl->py);
+  cudaFree(pl->bj_lu);
+  cudaFree(pl->bj_rowp);
+  cudaFree(pl->perm);
+  cudaFree(pl->pA_rp);
+  cudaFree(pl->pA_ci);
+  cudaFree(pl->pA_v);
   cudaFree(pl->st);
   cudaFree(pl->arr_mem);
   if (pl->h_st) cudaFreeHost(pl->h_st);
@@ -433,6 +476,56 @@ static int validate_params(const gmres_params* p) {
   if (p->poly_degree < 0) return GMRES_ERR_INVALID;
   if (p->poly_degree > GMRES_MAX_POLY_DEGREE) return GMRES_ERR_TOO_LARGE;
   if (p->cgs_kernel != GMRES_CGS_REGISTER && p->cgs_kernel != GMRES_CGS_TMA) return GMRES_ERR_INVALID;
+  if (p->bj_block < 0) return GMRES_ERR_INVALID;
+  if (p->bj_block > GMRES_MAX_BJ_BLOCK) return GMRES_ERR_TOO_LARGE;
+  if (p->bj_block > 0 && p->poly_degree > 0) return GMRES_ERR_INVALID;  // one preconditioner
+  return GMRES_OK;
+}
+
+// Reverse Cuthill-McKee reordering at plan creation (host, rcm_host.h): the plan keeps the
+// reordered CSR P A P^T (columns ascending in each row, stable for equal columns) and the
+// permutation, and solves (P A P^T)(P x) = P b.
+static int rcm_reorder(Plan& pl, const gmres_csr* A, cudaStream_t s) {
+  const int n = A->n, nnz = A->nnz;
+  std::vector<int32_t> rp((size_t)n + 1), ci((size_t)nnz), perm((size_t)n), iperm((size_t)n);
+  std::vector<double> va((size_t)nnz);
+  CK(cudaMemcpyAsync(rp.data(), A->row_ptr, 4 * rp.size(), cudaMemcpyDeviceToHost, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(ci.data(), A->col_idx, 4 * ci.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(va.data(), A->vals, 8 * va.size(), cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  rcm_order(n, rp.data(), ci.data(), perm.data());
+  for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
+  std::vector<int32_t> prp((size_t)n + 1, 0), pci((size_t)nnz);
+  std::vector<double> pva((size_t)nnz);
+  std::vector<std::pair<int32_t, int32_t>> row;  // (new column, position in the old row)
+  for (int i = 0; i < n; ++i) {
+    const int o = perm[i];
+    row.clear();
+    for (int32_t q = rp[o]; q < rp[o + 1]; ++q) row.emplace_back(iperm[ci[q]], q - rp[o]);
+    std::stable_sort(row.begin(), row.end(),
+                     [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                       return a.first < b.first;
+                     });
+    prp[i + 1] = prp[i] + (int32_t)row.size();
+    for (size_t t = 0; t < row.size(); ++t) {
+      pci[prp[i] + t] = row[t].first;
+      pva[prp[i] + t] = va[rp[o] + row[t].second];
+    }
+  }
+  CK(cudaMalloc((void**)&pl.pA_rp, 4 * prp.size()));
+  CK(cudaMalloc((void**)&pl.pA_ci, 4 * std::max<size_t>(pci.size(), 1)));
+  CK(cudaMalloc((void**)&pl.pA_v, 8 * std::max<size_t>(pva.size(), 1)));
+  CK(cudaMalloc((void**)&pl.perm, 4 * std::max<size_t>(perm.size(), 1)));
+  CK(cudaMemcpyAsync(pl.pA_rp, prp.data(), 4 * prp.size(), cudaMemcpyHostToDevice, s));
+  if (nnz) {
+    CK(cudaMemcpyAsync(pl.pA_ci, pci.data(), 4 * pci.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pl.pA_v, pva.data(), 8 * pva.size(), cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(pl.perm, perm.data(), 4 * perm.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  pl.A = gmres_csr{n, nnz, pl.pA_rp, pl.pA_ci, pl.pA_v};
   return GMRES_OK;
 }
 
@@ -454,7 +547,8 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   if (int e = validate_csr(A)) return e;
   if (int e = validate_params(p)) return e;
   if (kind < 0 || kind > 2) return GMRES_ERR_INVALID;
-  if (kind == 2 && p->poly_degree != 0) return GMRES_ERR_INVALID;  // FP32 GMRES: no polynomial
+  if (kind == 2 && (p->poly_degree != 0 || p->bj_block != 0 || p->bj_rcm != 0))
+    return GMRES_ERR_INVALID;  // FP32 GMRES: no preconditioner, no reordering
   if (A->n == 0) return GMRES_ERR_INVALID;  // an empty system has no plan (solves return OK)
   Plan* pl = new (std::nothrow) Plan();
   if (!pl) return GMRES_ERR_OOM;
@@ -474,6 +568,12 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   if (int e_ = CUDA_STATUS(cudaGetDevice(&dev))) return fail(e_);
   cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
   if (int e = check_csr_device(A, s)) return fail(e);
+  if (p->bj_rcm) {  // from here on the plan works on its reordered copy, pl->A
+    auto tr0 = std::chrono::steady_clock::now();
+    if (int e = rcm_reorder(*pl, A, s)) return fail(e);
+    pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tr0).count();
+  }
+  A = &pl->A;
 
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -572,7 +672,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, t0, t1);
-  pl->t_setup_ms = ms;
+  pl->t_setup_ms += ms;
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
 
@@ -603,6 +703,46 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
   }
 
+  // Block-Jacobi preconditioner: the diagonal blocks of A (the reordered copy when bj_rcm)
+  // factored once, in FP64, factors kept in the working type.
+  if (p->bj_block > 0) {
+    pl->bj = p->bj_block;
+    auto tb0 = std::chrono::steady_clock::now();
+    const long long nblocks = (pl->n + pl->bj - 1) / pl->bj;
+    if ((e = alloc(&pl->bj_lu, wb * (size_t)nblocks * pl->bj * pl->bj))) return fail(e);
+    if ((e = alloc((void**)&pl->bj_rowp, sizeof(int) * (size_t)pl->n))) return fail(e);
+    if ((e = alloc(&pl->pa, wb * (size_t)ld))) return fail(e);
+    if ((e = alloc(&pl->py, wb * (size_t)ld))) return fail(e);
+    int* d_bad = nullptr;
+    if ((e = alloc((void**)&d_bad, sizeof(int)))) return fail(e);
+    const int fgrid = (int)std::min<long long>(nblocks, (long long)pl->sms * 16);
+    dispatch(pl->prec, [&](auto PP) {
+      using W = typename Tr<decltype(PP)::value>::W;
+      k_bj_factor<W><<<fgrid, BJ_FACTOR_THREADS, 0, s>>>(A->row_ptr, A->col_idx, A->vals, pl->n,
+                                                         pl->bj, (W*)pl->bj_lu, pl->bj_rowp, d_bad);
+      return 0;
+    });
+    int bad = 0;
+    cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t ce = cudaStreamSynchronize(s);
+    cudaFree(d_bad);
+    if (int e_ = CUDA_STATUS(ce)) return fail(e_);
+    if (int e_ = CUDA_STATUS(cudaGetLastError())) return fail(e_);
+    if (bad) return fail(GMRES_ERR_INVALID);  // a singular diagonal block
+    const long long warps = pl->bj <= 32 ? (nblocks + 32 / pl->bj - 1) / (32 / pl->bj) : nblocks;
+    pl->grid_bj = (int)std::max<long long>(
+        1, std::min<long long>((warps + BJ_APPLY_WARPS - 1) / BJ_APPLY_WARPS, (long long)pl->sms * 32));
+    if (int e_ = CUDA_STATUS(cudaFuncSetAttribute(k_bj_apply<float>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  BJ_APPLY_WARPS * bj_slot(BJ_MAX) * 4)))
+      return fail(e_);
+    if (int e_ = CUDA_STATUS(cudaFuncSetAttribute(k_bj_apply<double>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  BJ_APPLY_WARPS * bj_slot(BJ_MAX) * 8)))
+      return fail(e_);
+    pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count();
+  }
+
   // Capture one restart cycle as a CUDA graph.
   if (int e_ = CUDA_STATUS(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking))) return fail(e_);
   if (int e_ = CUDA_STATUS(cudaEventCreate(&pl->ev0))) return fail(e_);
@@ -631,13 +771,26 @@ static void init_state(Plan& pl, DevState& h) {
   h.sigma = 1.0;
 }
 
+// b and x0 into the plan's vectors (through the permutation when the plan is reordered).
+static int load_rhs(Plan& pl, const double* b, const double* x0, cudaStream_t s) {
+  const size_t nb = sizeof(double) * (size_t)pl.n;
+  if (pl.perm) {
+    k_gather_perm<<<pl.grid_elem, NT, 0, s>>>(b, pl.perm, pl.n, pl.bb);
+    k_gather_perm<<<pl.grid_elem, NT, 0, s>>>(x0, pl.perm, pl.n, pl.xb);
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemcpyAsync(pl.bb, b, nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(pl.xb, x0, nb, cudaMemcpyDeviceToDevice, s));
+  }
+  return GMRES_OK;
+}
+
 int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStream_t s) {
   if (!b || !x) return GMRES_ERR_INVALID;
   const size_t nb = sizeof(double) * (size_t)pl.n;
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(pl.bb, b, nb, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(pl.xb, x, nb, cudaMemcpyDeviceToDevice, s));
+  if (int e = load_rhs(pl, b, x, s)) return e;
   CK(cudaEventRecord(pl.ev0, s));
   launch_residual(pl, 1, s);
   CK(cudaGetLastError());
@@ -654,8 +807,14 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
   CK(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const DevState& h = *pl.h_st;
-  if (h.zero_rhs) CK(cudaMemsetAsync(x, 0, nb, s));
-  else CK(cudaMemcpyAsync(x, pl.xb, nb, cudaMemcpyDeviceToDevice, s));
+  if (h.zero_rhs) {
+    CK(cudaMemsetAsync(x, 0, nb, s));
+  } else if (pl.perm) {
+    k_scatter_perm<<<pl.grid_elem, NT, 0, s>>>(pl.xb, pl.perm, pl.n, x);
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemcpyAsync(x, pl.xb, nb, cudaMemcpyDeviceToDevice, s));
+  }
   if (stats) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, pl.ev0, pl.ev1);
@@ -694,6 +853,22 @@ int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
   });
   if (e) return note_cuda((cudaError_t)e, __LINE__);
   CK(cudaStreamSynchronize(s));
+  return GMRES_OK;
+}
+
+// y = M^{-1} v with the plan's block-Jacobi factors (v: n doubles, y: n values of the
+// working type, both in the plan's numbering).  Asynchronous on s (two kernels).
+int plan_bj_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
+  if (!pl.bj || !v || !y) return GMRES_ERR_INVALID;
+  int e = dispatch(pl.prec, [&](auto PP) {
+    constexpr int P = decltype(PP)::value;
+    using W = typename Tr<P>::W;
+    k_load_work<P><<<pl.grid_elem, NT, 0, s>>>(v, (W*)pl.pa, pl.n);
+    k_bj_apply<W><<<pl.grid_bj, 32 * BJ_APPLY_WARPS, bj_smem<W>(pl), s>>>((const W*)pl.bj_lu, pl.bj_rowp, pl.n, pl.bj,
+                                             (const W*)pl.pa, (W*)y, nullptr, 0);
+    return (int)cudaGetLastError();
+  });
+  if (e) return note_cuda((cudaError_t)e, __LINE__);
   return GMRES_OK;
 }
 
@@ -762,11 +937,9 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
 // cycle did not reach.  The host reads the cycle flag after every step.
 int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_out, cudaStream_t s) {
   const int m = pl.m, nslots = 3 * m + 3;
-  const size_t nb = sizeof(double) * (size_t)pl.n;
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(pl.bb, b, nb, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(pl.xb, x0, nb, cudaMemcpyDeviceToDevice, s));
+  if (int e = load_rhs(pl, b, x0, s)) return e;
   launch_residual(pl, 1, s);
   std::vector<cudaEvent_t> ev(2 * (size_t)nslots, nullptr);
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -932,6 +1105,33 @@ int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* strea
   return gm::plan_poly_apply(*plan->pl, v, y, (cudaStream_t)stream);
 }
 
+int gmres_plan_bj_apply(gmres_plan plan, const double* v, void* y, void* stream) {
+  if (!plan) return GMRES_ERR_INVALID;
+  return gm::plan_bj_apply(*plan->pl, v, y, (cudaStream_t)stream);
+}
+
+int gmres_plan_perm(gmres_plan plan, int32_t* perm, int32_t* reordered) {
+  if (!plan || !reordered) return GMRES_ERR_INVALID;
+  const Plan& pl = *plan->pl;
+  *reordered = pl.perm != nullptr;
+  if (pl.perm && perm) {
+    CK(cudaMemcpy(perm, pl.perm, sizeof(int32_t) * (size_t)pl.n, cudaMemcpyDeviceToHost));
+  }
+  return GMRES_OK;
+}
+
+int gmres_rcm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* perm) {
+  if (n < 0 || (n > 0 && (!row_ptr || !col_idx || !perm))) return GMRES_ERR_INVALID;
+  if (n == 0) return GMRES_OK;
+  if (row_ptr[0] != 0) return GMRES_ERR_INVALID;
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return GMRES_ERR_INVALID;
+  for (int32_t q = 0; q < row_ptr[n]; ++q)
+    if (col_idx[q] < 0 || col_idx[q] >= n) return GMRES_ERR_INVALID;
+  gm::rcm_order(n, row_ptr, col_idx, perm);
+  return GMRES_OK;
+}
+
 int gmres_plan_poly_roots(gmres_plan plan, double* roots_re, double* roots_im, int32_t* nroots) {
   if (!plan || !nroots) return GMRES_ERR_INVALID;
   const Plan& pl = *plan->pl;
@@ -993,7 +1193,8 @@ int gmres_fd_solve(const gmres_csr* A, const double* b, double* x, const gmres_p
                    int64_t switch_iters, gmres_stats* stats_fp32, gmres_stats* stats_fp64,
                    void* stream) {
   if (int e = gm::validate_params(p)) return e;
-  if (switch_iters < 0 || p->poly_degree != 0) return GMRES_ERR_INVALID;
+  if (switch_iters < 0 || p->poly_degree != 0 || p->bj_block != 0 || p->bj_rcm != 0)
+    return GMRES_ERR_INVALID;
   // the switch happens at a restart: round up to whole cycles of the FP32 stage
   const int64_t m = p->restart_m;
   gmres_params q = *p;

@@ -88,6 +88,14 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(neg), ctypes.byref(st), None) == g.ERR_INVALID
     form = g.default_params(cgs_kernel=7)
     assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(form), ctypes.byref(st), None) == g.ERR_INVALID
+    for kw, code in ((dict(bj_block=-1), g.ERR_INVALID), (dict(bj_block=65), g.ERR_TOO_LARGE),
+                     (dict(bj_block=4, poly_degree=5), g.ERR_INVALID)):
+        q = g.default_params(**kw)
+        assert lib.gmres_ir_solve(ctypes.byref(c), 1, 1, ctypes.byref(q), ctypes.byref(st), None) == code
+    fd = g.default_params(bj_block=4)
+    assert lib.gmres_fd_solve(ctypes.byref(c), 1, 1, ctypes.byref(fd), 50, None, None, None) == g.ERR_INVALID
+    assert lib.gmres_plan_bj_apply(None, 1, 1, None) == g.ERR_INVALID
+    assert lib.gmres_plan_perm(None, None, None) == g.ERR_INVALID
     empty = g.csr_t(0, 0, None, None, None)
     assert lib.gmres_ir_solve(ctypes.byref(empty), 1, 1, ctypes.byref(p), ctypes.byref(st), None) == g.OK
 
