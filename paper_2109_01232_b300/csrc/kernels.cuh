@@ -241,8 +241,42 @@ __device__ __forceinline__ void dot_cols(const S* __restrict__ V, long long ld, 
   }
 }
 
+// Warp totals of 8 columns at once.  d[b] is this lane's term of column b; returns, in
+// every lane, the warp total of column (lane >> 2) & 7.  Each exchange (xor 16, 8, 4)
+// sends the half of the columns that the partner keeps, halving what a lane carries, then
+// two plain butterfly steps (xor 2, 1) finish: 9 shuffles instead of 8 x 5.  Every total
+// is formed by the same additions, with the same operands, as warp_sum of that column
+// (own value + partner's, partners xor 16, 8, 4, 2, 1), so the totals are bitwise
+// warp_sum's.
+template <class W>
+__device__ __forceinline__ W warp_sum8_cols(const W (&d)[8]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+  W h[4];  // columns 4 b4 + i
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const W send = b4 ? d[i] : d[4 + i];
+    const W keep = b4 ? d[4 + i] : d[i];
+    h[i] = keep + __shfl_xor_sync(full, send, 16);
+  }
+  W q[2];  // columns 4 b4 + 2 b3 + i
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const W send = b3 ? h[i] : h[2 + i];
+    const W keep = b3 ? h[2 + i] : h[i];
+    q[i] = keep + __shfl_xor_sync(full, send, 8);
+  }
+  const W send = b2 ? q[0] : q[1];
+  W v = (b2 ? q[1] : q[0]) + __shfl_xor_sync(full, send, 4);  // column 4 b4 + 2 b3 + b2
+  v += __shfl_xor_sync(full, v, 2);
+  v += __shfl_xor_sync(full, v, 1);
+  return v;
+}
+
 // Dot products of w with the columns V[c0..nc) for this thread's rows, summed over the
-// warp and added to acc[c] by lane 0.  EF: see update_cols.
+// warp and added to acc[c] by one lane per column (always the same lane for a column).
+// EF: see update_cols.
 template <bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long ld, long long base,
                                             int nc, const W (&wv)[VEC], W* acc, int c0 = 0) {
@@ -251,12 +285,8 @@ __device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long l
   for (; c + 8 <= nc; c += 8) {
     W d[8];
     dot_cols<8, EF>(V, ld, base, c, wv, d);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) d[b] = warp_sum(d[b]);
-    if (lane == 0) {
-#pragma unroll
-      for (int b = 0; b < 8; ++b) acc[c + b] += d[b];
-    }
+    const W t = warp_sum8_cols(d);
+    if ((lane & 3) == 0) acc[c + (lane >> 2)] += t;
   }
   for (; c < nc; ++c) {
     W d[1];
@@ -284,12 +314,8 @@ __device__ __forceinline__ void dots_to_acc_desc(const S* __restrict__ V, long l
   for (; c >= 8; c -= 8) {
     W d[8];
     dot_cols<8, false>(V, ld, base, c - 8, wv, d);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) d[b] = warp_sum(d[b]);
-    if (lane == 0) {
-#pragma unroll
-      for (int b = 0; b < 8; ++b) acc[c - 8 + b] += d[b];
-    }
+    const W t = warp_sum8_cols(d);
+    if ((lane & 3) == 0) acc[c - 8 + (lane >> 2)] += t;
   }
 }
 
