@@ -24,7 +24,7 @@ Strategies for GMRES on GPUs", arXiv 2109.01232):
   (see oracle/poly.py), or any M^{-1} given as a function (`right_prec`: block
   Jacobi, see oracle/precond.py), whose result is rounded to the working precision.
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
 * Convergence is measured by the explicit ||b - A x||_2 / ||b||_2 (Section
   3.1's definition).  FP64 GMRES ends a cycle early when the implicit residual
   |g_{j+1}| (Givens) reaches rtol*||b||, then confirms with the explicit one.

@@ -7,7 +7,7 @@ Method (Section 5.8 and its table of SuiteSparse runs; Section 3.4 for a single-
 preconditioner inside GMRES-IR): the matrix is reordered with a reverse Cuthill-McKee
 (RCM) ordering, then preconditioned with block Jacobi of block size k (the table's
 "J k"; k = 1 and k = 42 there), inside GMRES and GMRES-IR.  The paper gives no further
-detail, so the following readings are ours (each listed in the design doc):
+detail, so the following readings are ours:
 
 * RCM works on the structure of A + A^T without the diagonal.  deg(i) is the number of
   distinct neighbours of i.  Vertices are ranked by (deg, index).  Components are taken
