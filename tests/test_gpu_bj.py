@@ -162,3 +162,25 @@ def test_bj_full_workload_sampled_blocks(g, torch):
         z = np.linalg.solve(D, v[s:e])
         assert np.abs(y[s:e] - z).max() <= 2e-5 * np.abs(z).max()
     plan.close()
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (5, 42), (32, 32), (33, 33), (70, 64), (100, 7),
+                                 (97, 32), (130, 33)])
+def test_bj_apply_edge_sizes(g, torch, n, k):
+    """One row; a single block smaller than k; k at the boundary of the two warp layouts
+    (32: one block per warp in the packed form, 33: the two-rows-per-lane form); ragged
+    tails."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(n * 100 + k)
+    M = sp.random(n, n, density=min(1.0, 6.0 / n), random_state=n + k, format="csr")
+    M = (M + sp.diags(np.abs(M).sum(axis=1).A.ravel() + 1.0 + rng.random(n))).tocsr()
+    M.sort_indices()
+    p = gen.Problem("edge", n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                    M.data.astype(np.float64))
+    v = rng.standard_normal(n)
+    for kind, tol in (("gmres", 1e-12), ("ir", 1e-5)):
+        plan = g.Plan(g.DeviceCSR.from_problem(p), kind, restart_m=4, bj_block=k)
+        y = plan.bj_apply(torch.tensor(v, device="cuda")).double().cpu().numpy()
+        y_ref = pc.BlockJacobi(p, k).apply(v)
+        assert np.abs(y - y_ref).max() <= tol * np.abs(y_ref).max()
+        plan.close()
