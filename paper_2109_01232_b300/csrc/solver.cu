@@ -485,7 +485,7 @@ static int validate_params(const gmres_params* p) {
 // Reverse Cuthill-McKee reordering at plan creation (host, rcm_host.h): the plan keeps the
 // reordered CSR P A P^T (columns ascending in each row, stable for equal columns) and the
 // permutation, and solves (P A P^T)(P x) = P b.
-static int rcm_reorder(Plan& pl, const gmres_csr* A, cudaStream_t s) {
+static int rcm_reorder_impl(Plan& pl, const gmres_csr* A, cudaStream_t s) {
   const int n = A->n, nnz = A->nnz;
   std::vector<int32_t> rp((size_t)n + 1), ci((size_t)nnz), perm((size_t)n), iperm((size_t)n);
   std::vector<double> va((size_t)nnz);
@@ -527,6 +527,15 @@ static int rcm_reorder(Plan& pl, const gmres_csr* A, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));  // the host vectors go out of scope
   pl.A = gmres_csr{n, nnz, pl.pA_rp, pl.pA_ci, pl.pA_v};
   return GMRES_OK;
+}
+
+static int rcm_reorder(Plan& pl, const gmres_csr* A, cudaStream_t s) {
+  try {
+    return rcm_reorder_impl(pl, A, s);
+  } catch (const std::bad_alloc&) {  // host arrays of the reordering
+    cudaStreamSynchronize(s);
+    return GMRES_ERR_OOM;
+  }
 }
 
 // Device check of the CSR structure (once per plan).
@@ -1128,7 +1137,11 @@ int gmres_rcm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t
     if (row_ptr[i + 1] < row_ptr[i]) return GMRES_ERR_INVALID;
   for (int32_t q = 0; q < row_ptr[n]; ++q)
     if (col_idx[q] < 0 || col_idx[q] >= n) return GMRES_ERR_INVALID;
-  gm::rcm_order(n, row_ptr, col_idx, perm);
+  try {
+    gm::rcm_order(n, row_ptr, col_idx, perm);
+  } catch (const std::bad_alloc&) {
+    return GMRES_ERR_OOM;
+  }
   return GMRES_OK;
 }
 
