@@ -238,7 +238,8 @@ int gmres_plan_perm(gmres_plan plan, int32_t* perm, int32_t* reordered);
  * pseudo-peripheral vertex of the George-Liu iteration and is ordered by a breadth-first
  * search that takes unvisited neighbours in rank order; the whole order is reversed.
  * GMRES_ERR_INVALID for a malformed structure (row_ptr[0] != 0, decreasing row_ptr,
- * column out of range) or a NULL pointer with n > 0. */
+ * column out of range) or a NULL pointer with n > 0; GMRES_ERR_OOM when the host memory
+ * of the graph (about 8 bytes per stored entry) cannot be allocated. */
 int gmres_rcm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* perm);
 
 /* The plan's polynomial roots (HOST arrays of at least poly_degree+1 entries,
