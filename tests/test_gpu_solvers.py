@@ -270,3 +270,27 @@ def test_ir_gives_up_on_stalled_refinement():
     xb = torch.zeros_like(bb)
     res = g.BatchPlan(batch, autotune=False, restart_m=1).solve(bb, xb)
     assert list(res.status) == [g.NOT_CONVERGED] * 2 and list(res.outer) == [IR_STALL_LIMIT] * 2
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_resume_from_a_checkpoint_equals_one_solve(g, torch, prec):
+    """The IR state is x alone: a solve stopped by the iteration cap at a cycle boundary and
+    called again from its x (the remaining budget) takes the same steps as one solve, and
+    ends at the same x (every refinement step starts from the FP64 residual of x)."""
+    p = gen.conv_diff_3d(24, 10.0, (0.6, 0.8, 0.0))
+    b = gen.rhs_ones(p)
+    A = g.DeviceCSR.from_problem(p)
+    bt, x1 = _dev(torch, b, np.zeros(p.n))
+    one = g.gmres_ir_solve(A, bt, x1, restart_m=25, inner_prec=prec)
+    assert one.status == g.OK and one.outer >= 3
+    cut = 25 * (one.outer // 2)
+    x2 = torch.zeros_like(x1)
+    first = g.gmres_ir_solve(A, bt, x2, restart_m=25, inner_prec=prec, max_iters=cut)
+    assert first.status == g.NOT_CONVERGED and first.iters == cut
+    rest = g.gmres_ir_solve(A, bt, x2, restart_m=25, inner_prec=prec,
+                            max_iters=100000 - cut)
+    assert rest.status == g.OK
+    assert first.iters + rest.iters == one.iters
+    assert first.outer + rest.outer == one.outer
+    np.testing.assert_allclose(x2.cpu().numpy(), x1.cpu().numpy(), rtol=0, atol=1e-14 * float(
+        torch.abs(x1).max()))
