@@ -251,6 +251,17 @@ def test_full_size_3d_ir_and_fp64(g, torch, cube):
     assert out["ir"][0].iters <= out["gmres"][0].iters + 150
     xi, xg = out["ir"][1], out["gmres"][1]
     assert np.linalg.norm(xi - xg) / np.linalg.norm(xg) <= 1e-6
+    # the oracle's own full solve of this instance (recorded by oracle/record_iterations.py):
+    # the same number of refinement steps and of inner iterations, and the final explicit
+    # residual to 1% (the two sum in different orders)
+    import json
+    import os
+    rec = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                       "iterations_3d100.json")
+    ref = json.load(open(rec))["pe10"]
+    r = out["ir"][0]
+    assert (r.iters, r.outer) == (ref["iters"], ref["outer"])
+    assert r.relres == pytest.approx(ref["relres"], rel=1e-2)
 
 
 def test_ir_gives_up_on_stalled_refinement():
