@@ -150,7 +150,8 @@ int gmres_ir_solve(const gmres_csr* A, const double* b, double* x, const gmres_p
  * FP64 GMRES(m) (as gmres_solve) from that iterate for the remaining p->max_iters.
  * Pointers as in gmres_solve.  stats_fp32 / stats_fp64 (either may be NULL) describe the
  * two stages; the return value is the FP64 stage's status.  switch_iters = 0 is plain
- * FP64 GMRES; no polynomial preconditioner (p->poly_degree must be 0). */
+ * FP64 GMRES; no preconditioner or reordering (p->poly_degree, p->bj_block and p->bj_rcm
+ * must be 0, else GMRES_ERR_INVALID). */
 int gmres_fd_solve(const gmres_csr* A, const double* b, double* x, const gmres_params* p,
                    int64_t switch_iters, gmres_stats* stats_fp32, gmres_stats* stats_fp64,
                    void* stream);
@@ -168,8 +169,13 @@ int gmres_solve_host(const gmres_csr* A_host, const double* b, double* x,
 typedef struct gmres_plan_s* gmres_plan;
 
 /* kind: 0 = FP64 GMRES, 1 = GMRES-IR with p->inner_prec, 2 = GMRES entirely in FP32
- * (GMRES-FD's first stage; p->inner_prec ignored, no polynomial).  A's arrays must stay
- * valid until gmres_plan_destroy. */
+ * (GMRES-FD's first stage; p->inner_prec ignored, no polynomial, block Jacobi or
+ * reordering).  A's arrays must stay valid until gmres_plan_destroy.  Set-up on the
+ * stream: CSR check, the low-precision SELL-32 copy of A, with bj_rcm the reordering
+ * (host) and the plan's reordered copy, the polynomial roots, the block factors, the
+ * graph capture.  GMRES_ERR_INVALID for a malformed CSR, bad parameters or a singular
+ * diagonal block (bj_block > 0); GMRES_ERR_OOM / GMRES_ERR_CUDA on allocation / runtime
+ * failure (nothing is leaked). */
 int gmres_plan_create(gmres_plan* plan, const gmres_csr* A, int32_t kind, const gmres_params* p,
                       void* stream);
 int gmres_plan_solve(gmres_plan plan, const double* b, double* x, gmres_stats* stats,
