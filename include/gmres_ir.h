@@ -95,6 +95,10 @@ typedef struct {
   int32_t bj_rcm;           /* nonzero: reorder the system with reverse Cuthill-McKee at
                                plan creation (Section 5.8; before the blocks are taken);
                                b, x0 and x stay in the caller's numbering */
+  int32_t max_outer;        /* cap on the restart cycles (GMRES) / refinement steps
+                               (GMRES-IR) of a solve; 0 = none (max_iters alone).  A solve
+                               stopped by it returns GMRES_NOT_CONVERGED with x the last
+                               iterate.  Must be 0 for the batched solver. */
 } gmres_params;
 
 /* Forms of the two CGS2 update kernels (the same arithmetic per row; both produce the

@@ -46,7 +46,8 @@ class params_t(ctypes.Structure):
                 ("inner_prec", ctypes.c_int32), ("poly_degree", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32),
                 ("cgs_kernel", ctypes.c_int32), ("poly_in_fp32", ctypes.c_int32),
-                ("bj_block", ctypes.c_int32), ("bj_rcm", ctypes.c_int32)]
+                ("bj_block", ctypes.c_int32), ("bj_rcm", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32)]
 
 
 class stats_t(ctypes.Structure):

@@ -633,7 +633,8 @@ static int batch_create(BatchPlan** out, const gmres_csr_batch* A, const gmres_p
   if (int e = validate_params(p)) return e;
   if (p->restart_m > GMRES_BATCH_MAX_M) return GMRES_ERR_TOO_LARGE;
   if (p->inner_prec != GMRES_FP32 && p->inner_prec != GMRES_FP64) return GMRES_ERR_INVALID;
-  if (p->poly_degree != 0 || p->bj_block != 0 || p->bj_rcm != 0) return GMRES_ERR_INVALID;
+  if (p->poly_degree != 0 || p->bj_block != 0 || p->bj_rcm != 0 || p->max_outer != 0)
+    return GMRES_ERR_INVALID;
   if (A->nsys < 0) return GMRES_ERR_INVALID;
   const int nsys = A->nsys;
   if (nsys > 0 && (!A->row_off || !A->nnz_off || !A->row_ptr || !A->col_idx || !A->vals))

@@ -479,6 +479,7 @@ static int validate_params(const gmres_params* p) {
   if (p->bj_block < 0) return GMRES_ERR_INVALID;
   if (p->bj_block > GMRES_MAX_BJ_BLOCK) return GMRES_ERR_TOO_LARGE;
   if (p->bj_block > 0 && p->poly_degree > 0) return GMRES_ERR_INVALID;  // one preconditioner
+  if (p->max_outer < 0) return GMRES_ERR_INVALID;
   return GMRES_OK;
 }
 
@@ -806,7 +807,10 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
   int* h_stop = &pl.h_st->stop;
   CK(cudaMemcpyAsync(h_stop, &pl.st->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const long long max_cycles = pl.p.max_iters + 2;
+  // one cycle (= one refinement step of GMRES-IR, one restart of GMRES) per graph launch;
+  // max_outer > 0 caps their number on the host
+  long long max_cycles = pl.p.max_iters + 2;
+  if (pl.p.max_outer > 0) max_cycles = std::min<long long>(max_cycles, pl.p.max_outer);
   for (long long c = 0; !*h_stop && c < max_cycles; ++c) {
     CK(cudaGraphLaunch(pl.exec, s));
     CK(cudaMemcpyAsync(h_stop, &pl.st->stop, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -816,6 +820,8 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
   CK(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const DevState& h = *pl.h_st;
+  // a solve ended by the cycle cap has no decision from the device: not converged
+  const int status = h.stop ? h.status : (int)ST_NOT_CONVERGED;
   if (h.zero_rhs) {
     CK(cudaMemsetAsync(x, 0, nb, s));
   } else if (pl.perm) {
@@ -827,7 +833,7 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
   if (stats) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, pl.ev0, pl.ev1);
-    stats->status = h.status;
+    stats->status = status;
     stats->iters = h.iters;
     stats->outer_iters = h.outer;
     stats->rel_resid = h.relres;
@@ -842,7 +848,7 @@ int plan_solve(Plan& pl, const double* b, double* x, gmres_stats* stats, cudaStr
     }
   }
   CK(cudaStreamSynchronize(s));
-  return h.status;
+  return status;
 }
 
 // ---------------------------------------------------------------------------

@@ -89,7 +89,8 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     form = g.default_params(cgs_kernel=7)
     assert lib.gmres_solve(ctypes.byref(c), 1, 1, ctypes.byref(form), ctypes.byref(st), None) == g.ERR_INVALID
     for kw, code in ((dict(bj_block=-1), g.ERR_INVALID), (dict(bj_block=65), g.ERR_TOO_LARGE),
-                     (dict(bj_block=4, poly_degree=5), g.ERR_INVALID)):
+                     (dict(bj_block=4, poly_degree=5), g.ERR_INVALID),
+                     (dict(max_outer=-1), g.ERR_INVALID)):
         q = g.default_params(**kw)
         assert lib.gmres_ir_solve(ctypes.byref(c), 1, 1, ctypes.byref(q), ctypes.byref(st), None) == code
     fd = g.default_params(bj_block=4)
@@ -116,7 +117,8 @@ def test_batched_arguments_rejected_before_any_launch(lib):
     ro, no = np.array([0, 4], np.int64), np.array([0, 4], np.int64)
     one = g.csr_batch_t(1, ro.ctypes.data, no.ctypes.data, 1, 1, 1)
     for kw, code in ((dict(restart_m=g.BATCH_MAX_M + 1), g.ERR_TOO_LARGE),
-                     (dict(inner_prec="fp16"), g.ERR_INVALID), (dict(poly_degree=3), g.ERR_INVALID)):
+                     (dict(inner_prec="fp16"), g.ERR_INVALID), (dict(poly_degree=3), g.ERR_INVALID),
+                     (dict(bj_block=4), g.ERR_INVALID), (dict(max_outer=2), g.ERR_INVALID)):
         q = g.default_params(**{"restart_m": 30, **kw})
         assert lib.gmres_batch_plan_create(ctypes.byref(plan), ctypes.byref(one), ctypes.byref(q), 0,
                                            None) == code

@@ -182,6 +182,24 @@ def test_iteration_cap(g, torch, small):
     assert r.relres == pytest.approx(io.relres, rel=1e-9)
 
 
+def test_refinement_step_cap(g, torch, small):
+    """max_outer caps the cycles: GMRES-IR stops after that many refinement steps (and FP64
+    GMRES after that many restarts) with NOT_CONVERGED and the oracle's iterate after the
+    same number of steps."""
+    p, b, _ = small
+    A = g.DeviceCSR.from_problem(p)
+    for fn, kind in ((g.gmres_ir_solve, "ir"), (g.gmres_solve, "gmres")):
+        bt, xt = _dev(torch, b, np.zeros(p.n))
+        r = fn(A, bt, xt, restart_m=10, max_outer=2, rtol=1e-12)
+        assert r.status == g.NOT_CONVERGED and r.outer == 2 and r.iters == 20, (kind, r)
+        if kind == "ir":
+            _, io = oracle.gmres_ir(p, b, m=10, max_iters=20, rtol=1e-12, inner="fp32")
+        else:
+            _, io = oracle.gmres(p, b, m=10, max_iters=20, rtol=1e-12)
+        assert io.iters == 20 and r.relres == pytest.approx(io.relres, rel=1e-3)
+        assert _relres(p, b, xt.cpu().numpy()) == pytest.approx(r.relres, rel=1e-6)
+
+
 def test_singular_breakdown_and_tiny_systems(g, torch):
     S = gen.Problem("diag10", 2, np.array([0, 1, 1], np.int32), np.array([0], np.int32),
                     np.array([1.0]))
