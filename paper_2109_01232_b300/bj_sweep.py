@@ -12,6 +12,8 @@ bytes: v read and cast, the factors, the pivot order, v read again and z written
 solve is capped at 20,000 iterations.
 
     python -m paper_2109_01232_b300.bj_sweep
+    python -m paper_2109_01232_b300.bj_sweep --apply-only   # the ncu target: set-up of the
+        # k = 42 FP32 plan, then five M^{-1} v calls (a cast kernel and k_bj_apply each)
 """
 from __future__ import annotations
 
@@ -88,6 +90,26 @@ def table(rows) -> str:
     return "\n".join(out)
 
 
+def apply_only(calls: int = 5):
+    import torch
+
+    import gen
+    import paper_2109_01232_b300 as g
+    p, k = gen.config_bj()[0]
+    plan = g.Plan(g.DeviceCSR.from_problem(p), "ir", restart_m=50, inner_prec="fp32",
+                  bj_block=k, bj_rcm=1)
+    v = torch.tensor(np.random.default_rng(5).standard_normal(p.n), device="cuda")
+    for _ in range(calls):
+        plan.bj_apply(v)
+    torch.cuda.synchronize()
+    full, last = divmod(p.n, k)
+    print(f"{p.name}: n = {p.n}, k = {k}, factor values = {full * k * k + last * last}")
+    plan.close()
+
+
 if __name__ == "__main__":
-    rows = run(log=lambda r: print(r, file=sys.stderr, flush=True))
-    print(table(rows))
+    if "--apply-only" in sys.argv[1:]:
+        apply_only()
+    else:
+        rows = run(log=lambda r: print(r, file=sys.stderr, flush=True))
+        print(table(rows))
