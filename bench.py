@@ -374,7 +374,7 @@ def run_ours(args, rank, world, local_rank):
             e2e.append(time.perf_counter() - t0)
             assert r.status == g.OK
         h2d = 4 * (p.n + 1) + 12 * p.nnz + 16 * p.n
-        cpu = None if args.no_cpu_baseline else cpu_baseline(it["p"], it["b"], ir_iters["pe10"])
+        cpu = None if args.no_cpu_baseline else cpu_baseline(it["p"], it["b"])
         batched = None if args.no_batched else run_batched(g, torch, peak)
         out = {
             "metric": METRIC, "value": per_solve_s, "unit": "s", "n_gpus": world,
@@ -413,33 +413,76 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def _recorded_oracle_iters():
+def _recorded(key: str):
+    """The oracle's own solve of the 100^3 instance recorded by oracle/record_iterations.py
+    (iterations, cycles, seconds), or None."""
     rec = os.path.join(ROOT, "oracle", "iterations_3d100.json")
     if os.path.exists(rec):
-        d = json.load(open(rec)).get("pe10")
+        d = json.load(open(rec)).get(key)
         if d and d.get("status") == 0:
-            return int(d["iters"])
+            return d
     return None
 
 
-def cpu_baseline(p, b, gpu_iters: int):
-    """Oracle GMRES-IR on the host cores: a bounded sample of 10 Arnoldi steps of the first
-    cycle (plus the FP64 residuals), scaled by the iteration count to a time to solution."""
-    import oracle
-    sample_iters = 10
+def _time(fn) -> float:
     t0 = time.perf_counter()
-    oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", max_iters=sample_iters)
-    dt = time.perf_counter() - t0
-    iters, src = gpu_iters, "GPU GMRES-IR iteration count of the same instance"
-    rec = _recorded_oracle_iters()
-    if rec:
-        iters, src = rec, "the oracle's own recorded iteration count"
-    return {"value": dt / sample_iters * iters, "unit": "s", "cores": threads_used(),
-            "kind": "oracle",
-            "sample": f"oracle.gmres_ir (numpy FP64 with FP32 rounding) on the Pe 10 instance: "
-                      f"{sample_iters} Arnoldi steps of the first cycle took {dt:.2f} s, scaled "
-                      f"by {iters} iterations ({src}); early steps are cheaper than the cycle "
-                      f"average, so this under-estimates the CPU time"}
+    fn()
+    return time.perf_counter() - t0
+
+
+def oracle_cycle_s(p, b, fp64: bool) -> float:
+    """Seconds of ONE whole oracle cycle on the host: the FP64 residual of x0, one restart
+    cycle of 50 Arnoldi steps (CGS2, Givens, least squares), the update and the new residual
+    -- GMRES-IR with the FP32-emulated inner cycle, or FP64 GMRES(50).  Every cycle of a
+    solve does the same work, so a solve takes (cycles) x this."""
+    import oracle
+    if fp64:
+        return _time(lambda: oracle.gmres(p, b, m=M, rtol=RTOL, max_iters=M))
+    return _time(lambda: oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", max_iters=M))
+
+
+def small_case_oracle(one_thread: bool = True) -> dict:
+    """The plain-method small case (2D 64 x 64, Pe 10, b = A x_true): oracle FP64 GMRES(50)
+    and GMRES-IR (FP32 inner GMRES(50), inner tolerance 1e-4) solved to 1e-10, median of 3
+    full solves on all BLAS threads and on one."""
+    import gen
+    import oracle
+    from threadpoolctl import threadpool_limits
+    p, b, _ = gen.config_small_2d()
+    runs = {"fp64_gmres": lambda: oracle.gmres(p, b, m=M, rtol=RTOL),
+            "gmres_ir": lambda: oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", inner_rtol=1e-4)}
+    out = {}
+    for name, fn in runs.items():
+        out[name] = {"s_median_of_3": statistics.median(_time(fn) for _ in range(3)),
+                     "iters": int(fn()[1].iters)}
+        if one_thread:
+            with threadpool_limits(1):
+                out[name]["s_1_thread"] = statistics.median(_time(fn) for _ in range(3))
+    return out
+
+
+def cpu_baseline(p, b) -> dict:
+    """The oracle on the GPU machine's host cores (a bounded sample of about 20-30 s).  The
+    benchmark's Pe 10 instance: one whole GMRES-IR refinement step and one whole FP64
+    GMRES(50) cycle, each timed and multiplied by the number of cycles the oracle's own
+    full solve of that instance takes (oracle/iterations_3d100.json: 14 and the FP64
+    count).  Plus the small 64 x 64 case solved in full (median of 3, all threads and one)."""
+    rec_ir, rec_64 = _recorded("pe10"), _recorded("pe10_fp64")
+    t_ir = oracle_cycle_s(p, b, fp64=False)
+    t_64 = oracle_cycle_s(p, b, fp64=True)
+    n_ir = int(rec_ir["outer"]) if rec_ir else 14
+    n_64 = int(rec_64["outer"]) if rec_64 else None
+    small = small_case_oracle()
+    return {"value": t_ir * n_ir, "unit": "s", "cores": threads_used(), "kind": "oracle",
+            "fp64_gmres_s": t_64 * n_64 if n_64 else None,
+            "ir_cycle_s": t_ir, "fp64_cycle_s": t_64, "ir_cycles": n_ir, "fp64_cycles": n_64,
+            "small_64x64": small,
+            "sample": f"oracle.gmres_ir (numpy, FP32-emulated inner GMRES(50)) on the Pe 10 "
+                      f"100^3 instance: one whole refinement step (residual, 50 Arnoldi steps, "
+                      f"least squares, update, residual) took {t_ir:.2f} s, x {n_ir} steps of "
+                      f"the oracle's own full solve; FP64 GMRES(50): one cycle {t_64:.2f} s x "
+                      f"{n_64} cycles; 64x64 case: full solves.  The sparse products run on one "
+                      f"thread (numpy), the dense basis products on `cores` BLAS threads"}
 
 
 def threads_used() -> int:
@@ -453,23 +496,22 @@ def threads_used() -> int:
 
 # --------------------------------------------------------- reference arm ----
 def run_reference(args, rank):
+    """The reference arm: the CPU oracle on the host cores, on the benchmark's Pe 10 100^3
+    instance.  Every step times one whole oracle GMRES-IR refinement step (FP64 residual, one
+    FP32-emulated GMRES(50) cycle, update, residual); `value` is the mean step time x the
+    number of refinement steps of the oracle's own full solve of that instance."""
     if rank != 0:
         return None
     import gen
-    import oracle
     p, b = gen.config_3d(10.0)
-    iters = _recorded_oracle_iters()
-    sample_iters = 5
+    rec = _recorded("pe10")
+    n_cyc = int(rec["outer"]) if rec else 14
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", max_iters=sample_iters)
+        t = oracle_cycle_s(p, b, fp64=False)
         if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    per_iter = statistics.mean(times) / sample_iters
-    n_it = iters if iters else 1600
-    value = per_iter * n_it
-    src = "the oracle's recorded count" if iters else "a nominal 1600 iterations"
+            times.append(t)
+    value = statistics.mean(times) * n_cyc
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": False,
@@ -477,11 +519,33 @@ def run_reference(args, rank):
             "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": "s", "kind": "oracle",
                              "cores": threads_used(),
-                             "sample": f"each step: {sample_iters} oracle GMRES-IR Arnoldi steps "
-                                       f"(with set-up) on the Pe 10 instance, scaled by {n_it} "
-                                       f"iterations ({src})"},
+                             "sample": f"each step: one whole oracle GMRES-IR refinement step "
+                                       f"(50 Arnoldi steps) on the Pe 10 instance; x {n_cyc} "
+                                       f"steps of the oracle's own full solve"},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+def cpu_full(args) -> dict:
+    """Complete oracle solves of the Pe 10 100^3 instance (GMRES-IR and FP64 GMRES(50) to
+    1e-10), `--cpu-full-reps` each: several minutes per solve, so not part of the default
+    run.  Checks the whole-cycle samples of the default run against whole solves."""
+    import gen
+    import oracle
+    p, b = gen.config_3d(10.0)
+    out = {"cores": threads_used(), "workload": "Pe 10 100^3 instance, x0 = 0, rtol 1e-10"}
+    for name, fn in (("gmres_ir", lambda: oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32")),
+                     ("fp64_gmres", lambda: oracle.gmres(p, b, m=M, rtol=RTOL))):
+        ts, info = [], None
+        for _ in range(args.cpu_full_reps):
+            t0 = time.perf_counter()
+            _, info = fn()
+            ts.append(time.perf_counter() - t0)
+        out[name] = {"s": ts, "s_median": statistics.median(ts), "iters": int(info.iters),
+                     "cycles": int(info.outer), "relres": float(info.relres),
+                     "one_cycle_s": oracle_cycle_s(p, b, fp64=(name == "fp64_gmres"))}
+    out["small_64x64"] = small_case_oracle()
+    return out
 
 
 def main():
@@ -492,7 +556,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched workload")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="only time complete oracle solves on the host (minutes per solve)")
+    ap.add_argument("--cpu-full-reps", type=int, default=1)
     args = ap.parse_args()
+    if args.cpu_full:
+        print(json.dumps(cpu_full(args)))
+        return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     rank = int(os.environ.get("RANK", 0))

@@ -6,7 +6,7 @@ kernels read V three times): 1/3 flop per byte.  To run at the HBM copy bandwidt
 (8192^3, CUDA events, best of 5 after a warm-up; a library GEMM is the highest FP64 rate a
 kernel can expect) and the FP32 SGEMM rate for comparison, and prints which bound applies.
 
-    python -m paper_2109_01232_b300.fp64_rate
+    python fp64_rate.py
 """
 from __future__ import annotations
 

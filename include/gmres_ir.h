@@ -99,6 +99,16 @@ typedef struct {
                                (GMRES-IR) of a solve; 0 = none (max_iters alone).  A solve
                                stopped by it returns GMRES_NOT_CONVERGED with x the last
                                iterate.  Must be 0 for the batched solver. */
+  int64_t tma_wait_cycles;  /* bound, in SM clocks, of each wait of the TMA-fed CGS kernels
+                               (cgs_kernel = GMRES_CGS_TMA) for a stage of copies or a
+                               released stage; 0 = the default, 2^31 clocks (about a second).
+                               A wait that expires ends the solve with
+                               GMRES_ERR_DEVICE_TIMEOUT; the kernel still waits for the copies
+                               it has issued, with the default bound, before it returns */
+  int32_t tma_test_withhold; /* test hook of that timeout path, 0 in normal use: nonzero makes
+                               the TMA producer of every CGS launch issue the copies of its
+                               first row block only, so the consumers' wait for the second
+                               block can only end by the bound */
 } gmres_params;
 
 /* Forms of the two CGS2 update kernels (the same arithmetic per row; both produce the
@@ -282,19 +292,25 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream);
  * -- code whose GPU memory is owned by another allocator that reserved it up
  * front, latency-critical loops that cannot take the implicit device-wide
  * synchronisation of cudaMalloc/cudaFree, and plug-ins that may not allocate.
- * It runs the CSR form of the fused SpMV kernel behind gmres_plan_spmv (plans
- * use a SELL-32 copy of A, which this entry point cannot allocate), so y agrees
- * with gmres_plan_spmv on an FP64 plan to rounding; its scratch (the kernel's state, partial sums and
- * one vector of n doubles) lives in a fixed device array of about 8.1 MB that
- * every GPU loading this library keeps until the process exits.
+ * It runs the library's CSR SpMV kernel (plans use a SELL-32 copy of A, which
+ * this entry point cannot allocate; the products are summed in CSR order, so y
+ * agrees with gmres_plan_spmv on an FP64 plan to rounding).  Its scratch -- a
+ * device state with the flag of the structure check, and room to stage v when
+ * y overlaps it -- lives in a fixed device array of about 8 MB that every GPU
+ * loading this library keeps until the process exits.
  *   A: DEVICE CSR (FP64 values), n <= GMRES_NOALLOC_MAX_N, else
- *      GMRES_ERR_TOO_LARGE (checked before any device work).
- *   v: DEVICE, n doubles; y: DEVICE, n doubles (must not overlap v).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  All calls share the one array: calls that may overlap on
- * the GPU (different streams, or several host threads) race and must be
- * serialised by the caller.  Returns after the stream has finished the work. */
+ *      GMRES_ERR_TOO_LARGE (checked before any device work).  The structure is
+ *      checked on the device first (row_ptr[0] = 0, row_ptr[n] = nnz,
+ *      non-decreasing row_ptr, 0 <= col_idx < n): a malformed one returns
+ *      GMRES_ERR_INVALID with y untouched.
+ *   v: DEVICE, n doubles; y: DEVICE, n doubles.  y may overlap v (then v is
+ *      copied into the scratch array before the product).
+ * Each call looks up the array's address on the current device
+ * (cudaGetSymbolAddress) and returns only after the stream has finished the
+ * work, so the call is synchronous: it cannot be made on a stream that is
+ * being captured into a graph.  All calls share the one array: calls that may
+ * overlap on the GPU (different streams, or several host threads) race and
+ * must be serialised by the caller. */
 #define GMRES_NOALLOC_MAX_N (1 << 20)
 int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, double* y, void* stream);
 

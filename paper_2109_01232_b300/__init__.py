@@ -47,7 +47,8 @@ class params_t(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("record_history", ctypes.c_int32),
                 ("cgs_kernel", ctypes.c_int32), ("poly_in_fp32", ctypes.c_int32),
                 ("bj_block", ctypes.c_int32), ("bj_rcm", ctypes.c_int32),
-                ("max_outer", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("tma_wait_cycles", ctypes.c_int64),
+                ("tma_test_withhold", ctypes.c_int32)]
 
 
 class stats_t(ctypes.Structure):
@@ -445,7 +446,15 @@ def splitmix64(n: int, seed: int, stream=None):
 def spmv_fp64_noalloc(A: DeviceCSR, v, y, stream=None) -> None:
     """y = A v in FP64 through gmres_spmv_fp64_noalloc, which allocates no device memory
     (for callers whose GPU memory belongs to another allocator or that must not trigger
-    cudaMalloc's implicit synchronisation).  v, y: float64 CUDA tensors of length n."""
+    cudaMalloc's implicit synchronisation).  v, y: contiguous float64 CUDA tensors of at
+    least n entries on the current device; y may be v (in place).  Synchronous."""
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    for name, t in (("v", v), ("y", y)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError(f"{name} must be a float64 CUDA tensor")
+        if t.device.index != dev or not t.is_contiguous() or t.numel() < A.n:
+            raise ValueError(f"{name} must be contiguous, on the current device, with >= n entries")
     c = A.c()
     _check(lib().gmres_spmv_fp64_noalloc(ctypes.byref(c), _ptr(v), _ptr(y), _stream(stream)),
            "spmv_fp64_noalloc")

@@ -15,10 +15,13 @@
 // Prologues and partial-sum outputs are those of k_cgs_u1 / k_cgs_u2 (kernels.cuh), and
 // both run on the same grid, so either form can produce any step's partials.
 //
-// Every mbarrier wait is bounded (TMA_WAIT_CYCLES SM clocks, and an iteration cap).  If
-// one expires the kernel records ST_TIMEOUT and stops the solve; the other warps stop
-// waiting as soon as they see the error, the producer waits (bounded) for the copies it
-// issued, and the CTA returns without writing partial sums.
+// Every mbarrier wait is bounded (TmaWait::cycles SM clocks, TMA_WAIT_CYCLES by default,
+// and an iteration cap).  If one expires the kernel records ST_TIMEOUT and stops the
+// solve; the other warps stop waiting as soon as they see the error, the producer waits
+// for the copies it issued (bounded by TMA_WAIT_CYCLES whatever the first bound), and the
+// CTA returns without writing partial sums.  TmaWait::withhold (a test hook) makes the
+// producer issue only its first row block's copies, so the consumers' wait for the second
+// block can only end by the bound: the timeout path runs with no fault and no hang.
 #pragma once
 
 #include "kernels.cuh"
@@ -34,6 +37,11 @@ constexpr int TMA_U1_MAX_COLS = TMA_U1_ACC * TMA_CW;
 constexpr size_t TMA_SMEM_BUDGET = 108 * 1024;  // two CTAs per SM
 constexpr long long TMA_WAIT_CYCLES = 1LL << 31;  // about a second at the B300's SM clocks
 constexpr long long TMA_SPIN_LIMIT = 1LL << 28;
+
+struct TmaWait {
+  long long cycles;  // bound of the producer's and consumers' waits
+  bool withhold;     // test hook: copies of the first row block only
+};
 
 // Shared-memory layout of both kernels for a step with nc basis columns.
 template <int P>
@@ -84,17 +92,18 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Waits for the completion of the phase of parity `parity`.  Gives up (false) when the
-// time or iteration limit expires, or when *abort becomes non-zero (abort may be null).
+// Waits for the completion of the phase of parity `parity`.  Gives up (false) when
+// `cycles` SM clocks or the iteration limit have passed, or when *abort becomes non-zero
+// (abort may be null).
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
-                                          const int* abort) {
+                                          const int* abort, long long cycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (long long i = 1; i < TMA_SPIN_LIMIT; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 0) {
       if (abort && *(volatile const int*)abort) return false;
-      if (clock64() - t0 > TMA_WAIT_CYCLES) return false;
+      if (clock64() - t0 > cycles) return false;
     }
   }
   return false;
@@ -126,16 +135,17 @@ template <int P>
 __device__ __forceinline__ void tma_produce(const typename Tr<P>::S* __restrict__ V, long long ld,
                                             int nc, const typename Tr<P>::W* __restrict__ win,
                                             unsigned char* stages, int ns, TmaCtl& ctl,
-                                            long long b0, long long b1) {
+                                            long long b0, long long b1, TmaWait tw) {
   using L = TmaLayout<P>;
   if ((threadIdx.x & 31) == 0) {
     const size_t stage_bytes = L::stage(nc);
     long long issued = 0;
-    for (long long k = 0; k < b1 - b0; ++k) {
+    const long long nblk = tw.withhold ? (b1 - b0 < 1 ? b1 - b0 : 1) : b1 - b0;
+    for (long long k = 0; k < nblk; ++k) {
       if (*(volatile int*)&ctl.err) break;
       const int s = (int)(k % ns);
       const unsigned it = (unsigned)(k / ns);
-      if (k >= ns && !mbar_wait(&ctl.empty[s], (it - 1) & 1u, &ctl.err)) {
+      if (k >= ns && !mbar_wait(&ctl.empty[s], (it - 1) & 1u, &ctl.err, tw.cycles)) {
         *(volatile int*)&ctl.err = 1;
         break;
       }
@@ -150,7 +160,7 @@ __device__ __forceinline__ void tma_produce(const typename Tr<P>::S* __restrict_
     }
     // the copies into the last stages must land before the CTA exits
     for (long long k = issued > ns ? issued - ns : 0; k < issued; ++k)
-      mbar_wait(&ctl.full[k % ns], (unsigned)(k / ns) & 1u, nullptr);
+      mbar_wait(&ctl.full[k % ns], (unsigned)(k / ns) & 1u, nullptr, TMA_WAIT_CYCLES);
   }
   __syncwarp();
 }
@@ -158,8 +168,9 @@ __device__ __forceinline__ void tma_produce(const typename Tr<P>::S* __restrict_
 // Consumer side: waits for fill k of its stage.  Returns whether the stage may be used;
 // false once any wait of the CTA has failed (the result is the same on all lanes).  Every
 // consumer thread still runs the loop body for every block, so named barriers in it match.
-__device__ __forceinline__ bool tma_acquire(TmaCtl& ctl, long long k, int ns, bool valid) {
-  bool ok = valid && mbar_wait(&ctl.full[k % ns], (unsigned)(k / ns) & 1u, &ctl.err);
+__device__ __forceinline__ bool tma_acquire(TmaCtl& ctl, long long k, int ns, bool valid,
+                                            long long cycles) {
+  bool ok = valid && mbar_wait(&ctl.full[k % ns], (unsigned)(k / ns) & 1u, &ctl.err, cycles);
   ok = __all_sync(0xffffffffu, ok);
   if (!ok && valid && (threadIdx.x & 31) == 0) *(volatile int*)&ctl.err = 1;
   return ok;
@@ -205,7 +216,8 @@ template <int P>
 __global__ void __launch_bounds__(TMA_THREADS, 2) k_cgs_u1_tma(
     const typename Tr<P>::S* __restrict__ V, long long ld, int j, double v_scale,
     const typename Tr<P>::W* __restrict__ win, typename Tr<P>::W* __restrict__ wout,
-    StepParts<typename Tr<P>::W> parts, DevState* st, double* __restrict__ h1, int ns) {
+    StepParts<typename Tr<P>::W> parts, DevState* st, double* __restrict__ h1, int ns,
+    TmaWait tw) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   using L = TmaLayout<P>;
@@ -223,11 +235,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 2) k_cgs_u1_tma(
 #pragma unroll
   for (int q = 0; q < TMA_U1_ACC; ++q) dot[q] = W(0);
   if (warp == TMA_CW) {
-    tma_produce<P>(V, ld, nc, win, stages, ns, ctl, b0, b1);
+    tma_produce<P>(V, ld, nc, win, stages, ns, ctl, b0, b1, tw);
   } else {
     bool valid = true;
     for (long long k = 0; k < b1 - b0; ++k) {
-      valid = tma_acquire(ctl, k, ns, valid);
+      valid = tma_acquire(ctl, k, ns, valid, tw.cycles);
       const unsigned char* stg = stages + (size_t)(k % ns) * L::stage(nc);
       const S* Vs = reinterpret_cast<const S*>(stg);
       consumers_sync();  // every warp is done with the previous block's wsh
@@ -280,7 +292,8 @@ template <int P>
 __global__ void __launch_bounds__(TMA_THREADS, 2) k_cgs_u2_tma(
     const typename Tr<P>::S* __restrict__ V, long long ld, int j, double v_scale,
     const typename Tr<P>::W* __restrict__ win, typename Tr<P>::W* __restrict__ wout,
-    StepParts<typename Tr<P>::W> parts, DevState* st, double* __restrict__ h2, int ns) {
+    StepParts<typename Tr<P>::W> parts, DevState* st, double* __restrict__ h2, int ns,
+    TmaWait tw) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   using L = TmaLayout<P>;
@@ -296,11 +309,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 2) k_cgs_u2_tma(
   const long long b0 = cta_begin(nb, 1), b1 = cta_begin(nb, 1, 1);
   W nrm = W(0);
   if (warp == TMA_CW) {
-    tma_produce<P>(V, ld, nc, win, stages, ns, ctl, b0, b1);
+    tma_produce<P>(V, ld, nc, win, stages, ns, ctl, b0, b1, tw);
   } else {
     bool valid = true;
     for (long long k = 0; k < b1 - b0; ++k) {
-      valid = tma_acquire(ctl, k, ns, valid);
+      valid = tma_acquire(ctl, k, ns, valid, tw.cycles);
       if (valid) {
         const unsigned char* stg = stages + (size_t)(k % ns) * L::stage(nc);
         const S* Vs = reinterpret_cast<const S*>(stg);

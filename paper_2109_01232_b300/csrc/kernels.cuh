@@ -348,9 +348,12 @@ struct SpmvSmem {
 // PLAIN: src is already the vector to multiply (p(A) v_j with a polynomial
 // preconditioner, working type, unscaled): it is gathered as is and V[:, j], stored
 // by the polynomial's first kernel, is not written.
+// SPMV_ONLY (with PLAIN): w = A src and nothing else -- no dot products, no norm, no
+// partial sums; V, part and h1 are not touched (the kernel still reads st->stop and
+// returns at once when it is set).
 // The matrix is CSR (rp, ci, av); plans use the SELL-32 form k_spmv_sell below.
 // ---------------------------------------------------------------------------
-template <int P, class SrcT, bool PLAIN = false>
+template <int P, class SrcT, bool PLAIN = false, bool SPMV_ONLY = false>
 __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     const int* __restrict__ rp, const int* __restrict__ ci, const typename Tr<P>::S* __restrict__ av,
     int n, long long ld, double row_scale_d, const SrcT* __restrict__ src, double v_scale,
@@ -398,10 +401,11 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
       const int il = tid + k * NT;
       const int row = r0 + il;
       const W wv = (row < n) ? row_scale * a[k] : W(0);
-      w_s[il] = wv;
+      if constexpr (!SPMV_ONLY) w_s[il] = wv;
       if (row < n) wout[row] = wv;
     }
-    __syncthreads();
+    __syncthreads();  // every thread has read rp_s before the next tile rewrites it
+    if constexpr (SPMV_ONLY) continue;
     // First CGS pass, transposed GEMV: VEC consecutive rows per thread.
     const long long gb = (long long)r0 + tid * VEC;
     W wv[VEC];
@@ -415,6 +419,7 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     if (lane == 0) acc[warp * ncol + j + 1] += nrm;
     __syncthreads();
   }
+  if constexpr (SPMV_ONLY) return;
   const int G = gridDim.x;
   for (int c = tid; c < ncol; c += NT) {
     W s = W(0);
@@ -524,7 +529,8 @@ __device__ __forceinline__ bool cluster_column_sums(const ColF& col, int ncol, W
   __shared__ int s_flag, s_any;
   int flag = 0;
   if (threadIdx.x == 0) flag = skip_flag();
-  for (int c = rank + CL * warp; c < ncol; c += CL * NWARP) {
+  const int nw = blockDim.x >> 5;
+  for (int c = rank + CL * warp; c < ncol; c += CL * nw) {
     const ColumnSrc<W> src = col(c);
     const W v = warp_sum_partials(src.ptr, src.count);
     if (lane == 0) mine[c] = v;

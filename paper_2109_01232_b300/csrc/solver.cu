@@ -262,17 +262,19 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
     const int nc = j + 1;
     const int ns = pl.p.cgs_kernel == GMRES_CGS_TMA ? TmaLayout<P>::stages(nc) : 0;
     const size_t tb = TmaLayout<P>::bytes(nc, ns);
+    const TmaWait tw{pl.p.tma_wait_cycles > 0 ? pl.p.tma_wait_cycles : TMA_WAIT_CYCLES,
+                     pl.p.tma_test_withhold != 0};
     if (which == 1) {
       if (ns && nc <= TMA_U1_MAX_COLS)
         k_cgs_u1_tma<P><<<pl.grid_vec, TMA_THREADS, tb, s>>>(V, pl.ld, j, pl.v_scale, w1, w2, sp,
-                                                             pl.st, pl.arr.h1, ns);
+                                                             pl.st, pl.arr.h1, ns, tw);
       else
         k_cgs_u1<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)nc * (1 + NWARP), s>>>(
             V, pl.ld, j, pl.v_scale, w1, w2, sp, pl.st, pl.arr.h1);
     } else {
       if (ns)
         k_cgs_u2_tma<P><<<pl.grid_vec, TMA_THREADS, tb, s>>>(V, pl.ld, j, pl.v_scale, w2, w3, sp,
-                                                             pl.st, pl.arr.h2, ns);
+                                                             pl.st, pl.arr.h2, ns, tw);
       else
         k_cgs_u2<P><<<pl.grid_vec, NT, sizeof(W) * (size_t)nc, s>>>(V, pl.ld, j, pl.v_scale, w2,
                                                                     w3, sp, pl.st, pl.arr.h2);
@@ -480,6 +482,7 @@ static int validate_params(const gmres_params* p) {
   if (p->bj_block > GMRES_MAX_BJ_BLOCK) return GMRES_ERR_TOO_LARGE;
   if (p->bj_block > 0 && p->poly_degree > 0) return GMRES_ERR_INVALID;  // one preconditioner
   if (p->max_outer < 0) return GMRES_ERR_INVALID;
+  if (p->tma_wait_cycles < 0) return GMRES_ERR_INVALID;
   return GMRES_OK;
 }
 
@@ -1338,9 +1341,10 @@ int gmres_splitmix64_fill(double* out, int64_t n, uint64_t seed, void* stream) {
 // Some callers cannot call cudaMalloc: code whose device memory is owned by another
 // allocator that reserved the GPU up front, latency-critical loops that cannot afford
 // the implicit device synchronisation of cudaMalloc/cudaFree, and plug-ins that are not
-// allowed to allocate at all.  gmres_spmv_fp64_noalloc runs the CSR form of the fused
-// SpMV kernel behind gmres_plan_spmv (plans use a SELL-32 copy), with its scratch (the kernel's device state,
-// per-CTA partial sums and the basis column it writes) in the file-scope array below.
+// allowed to allocate at all.  gmres_spmv_fp64_noalloc runs the CSR SpMV kernel
+// (k_spmv_arnoldi with only its product, no basis store or dot products) and keeps its
+// scratch -- the device state whose stop flag the CSR check sets and the kernel reads,
+// and a staging copy of v for calls whose y overlaps v -- in the file-scope array below.
 // Every GPU that loads this library holds that array until the process exits.
 // ===========================================================================
 namespace gm {
@@ -1351,17 +1355,14 @@ constexpr long long kNoAllocRows =
     ((long long)GMRES_NOALLOC_MAX_N + TILE_MAX - 1) / TILE_MAX * TILE_MAX;
 
 struct NoAllocHead {
-  DevState st;                      // flags, scale and tickets read by the kernel
-  double h1[4];                     // the kernel's dot products (not returned)
-  double part[2 * kNoAllocGrid];    // per-CTA partial sums
+  DevState st;  // st.stop: nonzero when the CSR check found a malformed structure
 };
 constexpr size_t kNoAllocHeadBytes = (sizeof(NoAllocHead) + 255) / 256 * 256;
 constexpr size_t kNoAllocBytes = kNoAllocHeadBytes + sizeof(double) * (size_t)kNoAllocRows;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Clears what the kernel needs to start from zero (flags, reduction ticket) and sets the
-// source scale to 1, so the input vector is multiplied as given.
+// Clears the state (the stop flag above all), so a call never sees the last call's flags.
 __global__ void k_noalloc_reset(DevState* st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *st = DevState{};
@@ -1369,35 +1370,33 @@ __global__ void k_noalloc_reset(DevState* st) {
   }
 }
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-int g_noalloc_sms[kNoAllocMaxDevices] = {};
+__global__ void k_copy_f64(const double* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device and its SM count.  Looked up
+// on every call (cudaGetSymbolAddress, with the caller's device current), so a context
+// that was destroyed and re-created (cudaDeviceReset) never leaves a stale address.
 int noalloc_scratch(void** out, int* sms) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
     cudaGetLastError();
     return GMRES_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return GMRES_ERR_CUDA;
-    }
-    int count = 0;
-    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();
-      return GMRES_ERR_CUDA;
-    }
-    g_noalloc_sms[dev] = count > 0 ? count : 1;
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
   }
-  *out = g_noalloc_ptr[dev];
-  *sms = g_noalloc_sms[dev];
+  int count = 0;
+  if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  *out = p;
+  *sms = count > 0 ? count : 1;
   return GMRES_OK;
 }
 
@@ -1415,16 +1414,32 @@ extern "C" int gmres_spmv_fp64_noalloc(const gmres_csr* A, const double* v, doub
   if (int e = gm::noalloc_scratch(&base, &sms)) return e;
   cudaStream_t s = (cudaStream_t)stream;
   auto* head = reinterpret_cast<gm::NoAllocHead*>(base);
-  double* vcol = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + gm::kNoAllocHeadBytes);
-  constexpr int TR = gm::SpmvSmem<0>::TR;
-  const int ntiles = (A->n + TR - 1) / TR;
-  const int grid = std::max(1, std::min({ntiles, sms * 8, gm::kNoAllocGrid}));
+  double* stage = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + gm::kNoAllocHeadBytes);
+  const int n = A->n;
   gm::k_noalloc_reset<<<1, 1, 0, s>>>(&head->st);
-  gm::k_spmv_arnoldi<0, double><<<grid, gm::NT, gm::SpmvSmem<0>::bytes(2), s>>>(
-      A->row_ptr, A->col_idx, A->vals, A->n, gm::kNoAllocRows, 1.0, v, 1.0, vcol, 0, y,
-      head->part, &head->st, head->h1);
+  // a malformed structure sets st.stop, and the SpMV kernel then returns before any load
+  gm::k_check_csr<<<256, 256, 0, s>>>(A->row_ptr, A->col_idx, n, A->nnz, &head->st.stop);
+  const double* src = v;
+  const uintptr_t vb = (uintptr_t)v, yb = (uintptr_t)y, bytes = sizeof(double) * (uintptr_t)n;
+  if (vb < yb + bytes && yb < vb + bytes) {  // y overlaps v: multiply a staged copy of v
+    const int cgrid = std::max(1, std::min((n + 255) / 256, sms * 8));
+    gm::k_copy_f64<<<cgrid, 256, 0, s>>>(v, stage, n);
+    src = stage;
+  }
+  constexpr int TR = gm::SpmvSmem<0>::TR;
+  const int ntiles = (n + TR - 1) / TR;
+  const int grid = std::max(1, std::min({ntiles, sms * 8, gm::kNoAllocGrid}));
+  gm::k_spmv_arnoldi<0, double, true, true><<<grid, gm::NT, gm::SpmvSmem<0>::bytes(2), s>>>(
+      A->row_ptr, A->col_idx, A->vals, n, gm::kNoAllocRows, 1.0, src, 1.0, nullptr, 0, y,
+      nullptr, &head->st, nullptr);
   if (cudaGetLastError() != cudaSuccess) return GMRES_ERR_CUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? GMRES_OK : GMRES_ERR_CUDA;
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, &head->st.stop, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  return bad ? GMRES_ERR_INVALID : GMRES_OK;
 }
 
 // Batched GMRES-IR (many small systems, one persistent kernel).

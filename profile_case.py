@@ -4,7 +4,7 @@ The profiling target for ncu (`-k regex:<kernel> -s <skip> -c <count>`): plan se
 FP64 residual of x0 = 0 and one cycle of m Arnoldi steps launched one kernel at a time,
 printing the per-launch device times measured with CUDA events.
 
-    python -m paper_2109_01232_b300.profile_case [--side 100] [--prec fp32] [--m 50]
+    python profile_case.py [--side 100] [--prec fp32] [--m 50]
         [--cgs-kernel register|tma]
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ import sys
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():

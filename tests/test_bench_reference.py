@@ -24,7 +24,7 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["unit"] == "s" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
-    assert "recorded" in d["cpu_baseline"]["sample"]  # scaled by the oracle's own count
+    assert "own full solve" in d["cpu_baseline"]["sample"]  # scaled by the oracle's own count
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 

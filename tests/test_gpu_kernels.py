@@ -78,49 +78,91 @@ def _basis(V, pm):
     return V.double().cpu().numpy().T / pm.s_v
 
 
-@pytest.mark.parametrize("which", ["2d", "3d"])
+def _norm_inf(p):
+    """||A||_inf (largest absolute row sum) from the CSR arrays."""
+    rows = np.repeat(np.arange(p.n), np.diff(p.row_ptr))
+    return float(np.bincount(rows, weights=np.abs(p.vals), minlength=p.n).max())
+
+
+# n >= 10^4 with a ragged tail: the SELL kernels run many slices per warp tile, many CTAs
+# per launch and a partial last tile (16,900 and 19,683 are no multiple of 32 VEC rows).
+LARGE = {
+    "2d130": lambda: gen.conv_diff_2d(130, 25.0, (0.6, 0.8)),
+    "3d27": lambda: gen.conv_diff_3d(27, 10.0, (1.0, -2.0, 0.5)),
+}
+
+
+def _column_errors(Vg, H, Vo, Ho, nA):
+    """Per column c: ||V_gpu[:, c] - V_oracle[:, c]||_2 and ||H_gpu[:, c] - H_oracle[:, c]||_2
+    / ||A||_inf (the Hessenberg column c has c + 2 entries)."""
+    k = H.shape[1]
+    dV = np.linalg.norm(Vg[:, :k + 1] - Vo[:, :k + 1], axis=0)
+    dH = np.array([np.linalg.norm(H[:c + 2, c] - Ho[:c + 2, c]) for c in range(k)]) / nA
+    return dV, dH
+
+
+@pytest.mark.parametrize("which", ["2d", "3d", "2d130", "3d27"])
 def test_arnoldi_fp64_matches_oracle(g, torch, which):
-    p = PROBLEMS[which]()
-    steps = 30
+    """FP64 Arnoldi/CGS2 (Algorithm 1, Section 3.1) against the oracle, every column of V
+    and H to 1e-13 (normwise, H relative to ||A||).  The two differ only in the order of
+    their sums; measured on a B300 the gap grows from ~1e-16 to ~4e-15 (V) and stays below
+    2e-16 ||A|| (H) over 50 steps, the same size as the oracle's own spread when its start
+    vector is perturbed by one unit roundoff."""
+    p = (PROBLEMS.get(which) or LARGE[which])()
+    steps = 30 if which in PROBLEMS else 50
     A, plan = _plan(g, p, "fp64", m=steps)
     v0 = oracle.splitmix64_uniform(5, p.n)
     V, H, k = plan.arnoldi(torch.tensor(v0, device="cuda"), steps)
     op = lambda v: oracle.spmv(p, v)
     Vo, Ho, ko = oracle.arnoldi(op, v0, steps)
     assert k == ko == steps
-    M = oracle.dense(p)
-    nA = np.linalg.norm(M, 2)
+    nA = _norm_inf(p)
     Vg = V.cpu().numpy().T
-    # elementwise parity with the oracle's Arnoldi (FP64, different summation order)
-    assert np.abs(H - Ho).max() <= 1e-12 * nA
-    assert np.abs(Vg - Vo).max() <= 1e-11
-    # Arnoldi relation and orthogonality of the GPU basis
-    assert np.linalg.norm(M @ Vg[:, :k] - Vg @ H, 2) / nA <= 1e-12
-    assert np.linalg.norm(np.eye(k + 1) - Vg.T @ Vg, 2) <= 1e-12
+    dV, dH = _column_errors(Vg, H, Vo, Ho, nA)
+    assert dV.max() <= 1e-13, dV
+    assert dH.max() <= 1e-13, dH
+    if p.n <= 6000:  # Arnoldi relation and orthogonality of the GPU basis (dense check)
+        M = oracle.dense(p)
+        n2 = np.linalg.norm(M, 2)
+        assert np.linalg.norm(M @ Vg[:, :k] - Vg @ H, 2) / n2 <= 1e-12
+        assert np.linalg.norm(np.eye(k + 1) - Vg.T @ Vg, 2) <= 1e-12
     plan.close()
 
 
-@pytest.mark.parametrize("prec,orth_tol,rel_tol,h_tol", [
-    ("fp32", 1e-5, 1e-5, 1e-5), ("fp16", 3e-2, 3e-3, 3e-3), ("bf16", 2e-1, 3e-2, 3e-2)])
-def test_arnoldi_low_precision(g, torch, prec, orth_tol, rel_tol, h_tol):
-    p = PROBLEMS["2d"]()
-    steps = 20
+# Bounds per column against the emulated oracle (same stored roundings, FP32 or FP64 sums in
+# a different order).  Measured on a B300 over 50 steps at n = 16,900 / 19,683: FP32 V 1.9e-6,
+# H 1.2e-8 ||A||; FP16 V 1.5e-3 (~3 u_fp16), H 7.6e-6 ||A||; BF16 V 1.1e-2 (~3 u_bf16),
+# H 3.7e-5 ||A||.  A stored value that rounds to the other neighbour on one side moves that
+# entry by one unit of the storage format, and the later steps inherit it, so V's bound is a
+# small multiple of the storage unit roundoff and grows with the step.
+@pytest.mark.parametrize("prec,v_tol,h_tol", [
+    ("fp32", 1e-5, 1e-5), ("fp16", 1e-2, 1e-4), ("bf16", 5e-2, 3e-4)])
+@pytest.mark.parametrize("which", list(LARGE))
+def test_arnoldi_low_precision(g, torch, which, prec, v_tol, h_tol):
+    p = LARGE[which]()
+    steps = 50
     A, plan = _plan(g, p, prec, m=steps)
-    v0 = oracle.splitmix64_uniform(6, p.n)
+    v0 = oracle.splitmix64_uniform(5, p.n)
     V, H, k = plan.arnoldi(torch.tensor(v0, device="cuda"), steps)
     assert k == steps
     pm = oracle.Precision.for_inner(prec, p)
     Vg = _basis(V, pm)
-    M = oracle.dense(p)
-    nA = np.linalg.norm(M, 2)
-    assert np.linalg.norm(np.eye(k + 1) - Vg.T @ Vg, 2) <= orth_tol
-    assert np.linalg.norm(M @ Vg[:, :k] - Vg @ H, 2) / nA <= rel_tol
-    # the oracle's emulated low-precision Arnoldi on the same input agrees on H
     a_low = pm.matrix_values(p.vals)
     op = lambda v: pm.rw(pm.s_A * oracle.spmv(p, v, a_low))
-    _, Ho, ko = oracle.arnoldi(op, v0, steps, pm)
+    Vo, Ho, ko = oracle.arnoldi(op, v0, steps, pm)
     assert ko == k
-    assert np.abs(H[:6, :5] - Ho[:6, :5]).max() <= h_tol * nA
+    nA = _norm_inf(p)
+    dV, dH = _column_errors(Vg, H, Vo, Ho, nA)
+    assert dV.max() <= v_tol, dV
+    assert dH.max() <= h_tol, dH
+    # the GPU basis is orthonormal to the storage precision (CGS2) and satisfies the
+    # Arnoldi relation with the stored copy of A; the oracle's emulated basis reaches
+    # 1.7 u_s and 0.33 u_s on these problems
+    u_s = oracle.unit_roundoff(prec)
+    G = Vg.T @ Vg
+    assert np.abs(np.eye(k + 1) - G).max() <= 16 * u_s
+    AV = np.stack([pm.s_A * oracle.spmv(p, Vg[:, c], a_low) for c in range(k)], axis=1)
+    assert np.linalg.norm(AV - Vg @ H) / (nA * np.sqrt(k)) <= 4 * u_s
     plan.close()
 
 
@@ -138,7 +180,7 @@ def test_arnoldi_cgs_kernel_forms_agree(g, torch, prec, steps, tol):
     kind = "gmres" if prec == "fp64" else "ir"
     ip = prec if prec != "fp64" else "fp32"
     Hs = []
-    for form in ("tma", "register"):
+    for form in ("register", "tma"):
         plan = g.Plan(A, kind, restart_m=steps, inner_prec=ip, cgs_kernel=form)
         V, H, k = plan.arnoldi(v0, steps)
         assert k == steps
@@ -147,7 +189,8 @@ def test_arnoldi_cgs_kernel_forms_agree(g, torch, prec, steps, tol):
     nA = np.abs(oracle.dense(p)).sum(axis=1).max()
     # the first steps agree to the working precision; later ones drift apart at most as
     # fast as the Arnoldi process amplifies rounding in the low-precision basis
-    assert np.abs(Hs[0][:9, :8] - Hs[1][:9, :8]).max() <= tol * nA
+    for H in Hs[1:]:
+        assert np.abs(Hs[0][:9, :8] - H[:9, :8]).max() <= tol * nA
     for H in Hs:
         assert np.isfinite(H).all()
 

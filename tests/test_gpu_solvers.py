@@ -93,6 +93,27 @@ def test_ir_half_storage(g, torch, prec):
     assert abs(res.iters - io.iters) <= 2 * 30 + io.iters // 4
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_ir_half_storage_solution_matches_oracle(g, torch, prec):
+    """GMRES-IR with FP16/BF16 storage reaches the FP64 solution: solved to 1e-12 on the
+    48 x 48 system (kappa ~ 1e3, so kappa * 1e-12 < 1e-8), x agrees with the oracle's
+    emulated GMRES-IR of the same storage precision, with the oracle's FP64 GMRES solved to
+    1e-13 and with the manufactured solution, each to 1e-8 (Algorithm 2: the refinement
+    recovers FP64 accuracy whatever the inner storage)."""
+    p, b, x_true = gen.config_small_2d(48)
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = g.gmres_ir_solve(A, bt, xt, restart_m=30, rtol=1e-12, inner_prec=prec)
+    assert res.status == g.OK and res.relres <= 1e-12
+    x = xt.cpu().numpy()
+    assert _relres(p, b, x) <= 1.0001e-12
+    x_ir, i_ir = oracle.gmres_ir(p, b, m=30, rtol=1e-12, inner=prec)
+    x_64, _ = oracle.gmres(p, b, m=30, rtol=1e-13)
+    for ref in (x_ir, x_64, x_true):
+        assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-8
+    assert abs(res.iters - i_ir.iters) <= 2 * 30 + i_ir.iters // 4
+
+
 def test_ir_inner_tolerance(g, torch, small):
     p, b, _ = small
     A = g.DeviceCSR.from_problem(p)
