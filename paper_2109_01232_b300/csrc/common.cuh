@@ -18,12 +18,15 @@ constexpr int TILE_MAX = 4096;    // largest SpMV row tile; every buffer's leadi
                                   // is a multiple of it, so tiles never cross the padding
 
 // Precision of the inner cycle: S = storage type of the Krylov basis and of the
-// copy of A, W = working (accumulation) type, VEC = rows per 16-byte vector of S.
+// copy of A, W = working (accumulation) type, VEC = rows per 16-byte vector of S (the
+// CGS update kernels' unit of a thread), VT = rows per lane in the SpMV kernel's dot
+// products (its warp tile is VT slices of 32 rows: 128 rows in every low precision; with
+// 256-row tiles in FP16/BF16 a CTA had fewer tiles than warps on 10^6 rows).
 template <int P> struct Tr;
-template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2; };
-template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4; };
-template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8; };
-template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8; };
+template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2, VT = 2; };
+template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4; };
+template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4; };
+template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4; };
 
 // storage -> working type
 __device__ __forceinline__ double to_w(double v) { return v; }
@@ -43,32 +46,55 @@ template <> __device__ __forceinline__ __half to_s<__half>(float v) { return __f
 template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// N consecutive elements through 16-byte loads/stores (p must be 16-byte aligned).
+// N consecutive elements through one or more 16-byte accesses, or one 8-byte access when
+// the vector is 8 bytes (p aligned to the vector's size, at most 16).
+template <class T, int N>
+struct VecBits {
+  static constexpr int BYTES = (int)(sizeof(T) * N);
+  static_assert(BYTES % 16 == 0 || BYTES == 8, "vector must be 8 bytes or a multiple of 16");
+  static constexpr bool WIDE = BYTES % 16 == 0;
+  static constexpr int Q = WIDE ? BYTES / 16 : 1;
+};
 template <class T, int N>
 __device__ __forceinline__ void ldv(const T* __restrict__ p, T (&o)[N]) {
-  static_assert((sizeof(T) * N) % 16 == 0, "vector must be a multiple of 16 bytes");
-  constexpr int Q = (int)(sizeof(T) * N / 16);
-  uint4 u[Q];
+  using VB = VecBits<T, N>;
+  if constexpr (VB::WIDE) {
+    uint4 u[VB::Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) u[q] = reinterpret_cast<const uint4*>(p)[q];
-  memcpy(o, u, sizeof(u));
+    for (int q = 0; q < VB::Q; ++q) u[q] = reinterpret_cast<const uint4*>(p)[q];
+    memcpy(o, u, sizeof(u));
+  } else {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    memcpy(o, &u, sizeof(u));
+  }
 }
 template <class T, int N>
 __device__ __forceinline__ void stv(T* __restrict__ p, const T (&o)[N]) {
-  constexpr int Q = (int)(sizeof(T) * N / 16);
-  uint4 u[Q];
-  memcpy(u, o, sizeof(u));
+  using VB = VecBits<T, N>;
+  if constexpr (VB::WIDE) {
+    uint4 u[VB::Q];
+    memcpy(u, o, sizeof(u));
 #pragma unroll
-  for (int q = 0; q < Q; ++q) reinterpret_cast<uint4*>(p)[q] = u[q];
+    for (int q = 0; q < VB::Q; ++q) reinterpret_cast<uint4*>(p)[q] = u[q];
+  } else {
+    uint2 u;
+    memcpy(&u, o, sizeof(u));
+    *reinterpret_cast<uint2*>(p) = u;
+  }
 }
 // Streaming load of data that is read once per kernel (evict-first in L1/L2).
 template <class T, int N>
 __device__ __forceinline__ void ldv_stream(const T* __restrict__ p, T (&o)[N]) {
-  constexpr int Q = (int)(sizeof(T) * N / 16);
-  uint4 u[Q];
+  using VB = VecBits<T, N>;
+  if constexpr (VB::WIDE) {
+    uint4 u[VB::Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q) u[q] = __ldcs(reinterpret_cast<const uint4*>(p) + q);
-  memcpy(o, u, sizeof(u));
+    for (int q = 0; q < VB::Q; ++q) u[q] = __ldcs(reinterpret_cast<const uint4*>(p) + q);
+    memcpy(o, u, sizeof(u));
+  } else {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+    memcpy(o, &u, sizeof(u));
+  }
 }
 
 // L2 evict-first loads for data that the kernel reads for the last time before other
@@ -82,15 +108,23 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
 }
 template <class T, int N>
 __device__ __forceinline__ void ldv_evict_first(const T* __restrict__ p, T (&o)[N]) {
-  constexpr int Q = (int)(sizeof(T) * N / 16);
+  using VB = VecBits<T, N>;
   const unsigned long long pol = l2_evict_first_policy();
-  uint4 u[Q];
+  if constexpr (VB::WIDE) {
+    uint4 u[VB::Q];
 #pragma unroll
-  for (int q = 0; q < Q; ++q)
-    asm("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-        : "=r"(u[q].x), "=r"(u[q].y), "=r"(u[q].z), "=r"(u[q].w)
-        : "l"(reinterpret_cast<const uint4*>(p) + q), "l"(pol));
-  memcpy(o, u, sizeof(u));
+    for (int q = 0; q < VB::Q; ++q)
+      asm("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=r"(u[q].x), "=r"(u[q].y), "=r"(u[q].z), "=r"(u[q].w)
+          : "l"(reinterpret_cast<const uint4*>(p) + q), "l"(pol));
+    memcpy(o, u, sizeof(u));
+  } else {
+    uint2 u;
+    asm("ld.global.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+        : "=r"(u.x), "=r"(u.y)
+        : "l"(reinterpret_cast<const uint2*>(p)), "l"(pol));
+    memcpy(o, &u, sizeof(u));
+  }
 }
 // ldv (EF = false) or ldv_evict_first (EF = true).
 template <bool EF, class T, int N>

@@ -738,14 +738,14 @@ __device__ void finalize_step(DevState* st, const Arrays& a, int js, double hn2,
 template <int P>
 struct SellSmem {
   using W = typename Tr<P>::W;
-  static constexpr int WT = 32 * Tr<P>::VEC;
+  static constexpr int WT = 32 * Tr<P>::VT;
   static size_t bytes(int ncol) { return sizeof(W) * (size_t)NWARP * (WT + ncol) + 16; }
 };
 
 // Step kernel 1 (see above).  A warp owns "warp tiles" of WT = 32 VEC consecutive rows
-// (VEC slices): it stores its rows of V[:, j], computes its rows of w = A v_j slice by
-// slice, turns them from the slice layout (lane l holds rows 32q + l) into the vector
-// layout (lane l holds rows VEC l .. VEC l + VEC-1) through a warp-private buffer, and
+// (VEC = Tr<P>::VT slices): it stores its rows of V[:, j], computes its rows of w = A v_j
+// slice by slice, turns them from the slice layout (lane l holds rows 32q + l) into the
+// vector layout (lane l holds rows VEC l .. VEC l + VEC-1) through a warp-private buffer, and
 // accumulates the first-pass dot products over its rows.  There is no CTA barrier inside
 // the loop, so warps at different phases overlap.  Each CTA owns an equal contiguous
 // range of warp tiles (cta_begin).  PLAIN: src is p(A) v_j (working type, unscaled),
@@ -758,7 +758,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     StepParts<typename Tr<P>::W> parts, DevState* st, Arrays arr) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  constexpr int VEC = Tr<P>::VEC;
+  constexpr int VEC = Tr<P>::VT;
   constexpr int WT = SellSmem<P>::WT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double gsh[GIVENS_SH];
