@@ -146,6 +146,38 @@ def roofline(ms: np.ndarray, n: int, nnz: int, prec: int):
     return dom, out
 
 
+KERNEL_CLASSES = {  # the paper's kernel classes (Section 5.2) in this fused design
+    "spmv": "SpMV + v_j store + first-pass GEMV-T (dots), Givens of the previous step",
+    "u1": "first-pass GEMV-N (update) + second-pass GEMV-T (dots)",
+    "u2": "second-pass GEMV-N (update) + norm",
+    "lsq": "least squares (FP64, both)",
+    "xupd": "x += gamma V y",
+    "residual": "FP64 residual r = b - A x",
+}
+
+
+def per_kernel_speedup(k_ir: dict, k_64: dict) -> dict:
+    """Per-cycle device time of each kernel class in GMRES-IR (FP32 inner) and FP64 GMRES on
+    the same instance, and their ratio (Section 5.2's per-kernel speed-up table)."""
+    out = {}
+    for name, what in KERNEL_CLASSES.items():
+        a, b = k_ir.get(name), k_64.get(name)
+        if a and b and a["ms_total"] > 0:
+            out[name] = {"what": what, "ir_ms": round(a["ms_total"], 4),
+                         "fp64_ms": round(b["ms_total"], 4),
+                         "speedup": round(b["ms_total"] / a["ms_total"], 3)}
+    t_ir = sum(v["ms_total"] for v in k_ir.values())
+    t_64 = sum(v["ms_total"] for v in k_64.values())
+    ortho = [c for c in ("u1", "u2") if c in k_ir and c in k_64]
+    o_ir = sum(k_ir[c]["ms_total"] for c in ortho)
+    o_64 = sum(k_64[c]["ms_total"] for c in ortho)
+    out["ortho_updates"] = {"what": "u1 + u2", "ir_ms": round(o_ir, 4), "fp64_ms": round(o_64, 4),
+                            "speedup": round(o_64 / o_ir, 3) if o_ir else None}
+    out["total"] = {"what": "one 50-step cycle, kernel by kernel", "ir_ms": round(t_ir, 4),
+                    "fp64_ms": round(t_64, 4), "speedup": round(t_64 / t_ir, 3) if t_ir else None}
+    return out
+
+
 # ------------------------------------------------------ measured traffic ----
 PROFILE_OF = {"spmv": "k_spmv_sell_3d100_fp32.md", "u1": "k_cgs_u1_3d100_fp32.md",
               "u2": "k_cgs_u2_3d100_fp32.md"}
@@ -360,6 +392,13 @@ def run_ours(args, rank, world, local_rank):
         plan.close()
         dom, kernels = roofline(ms, info["n"], info["nnz"], 1)
         kd = kernels[dom]
+        # the same cycle in FP64 GMRES(50): per-kernel IR over FP64 (Section 5.2's table)
+        plan = g.Plan(it["A"], "gmres", **kw)
+        plan.profile_cycle(it["bt"], x0)
+        ms64 = plan.profile_cycle(it["bt"], x0)
+        plan.close()
+        _, kernels64 = roofline(ms64, info["n"], info["nnz"], 0)
+        kernel_speedup = per_kernel_speedup(kernels, kernels64)
         # end to end through the host-pointer C ABI (copies in and out, plan creation)
         p = it["p"]
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -399,6 +438,7 @@ def run_ours(args, rank, world, local_rank):
                          "avg_launch_ms": kd["ms_total"] / kd["launches"]},
             "kernels": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv)
                             for kk, vv in v.items()} for k, v in kernels.items()},
+            "kernel_speedup_vs_fp64": kernel_speedup,
             "cpu_baseline": cpu,
             "batched": batched,
             "e2e": {"value": statistics.median(e2e), "unit": "s",

@@ -24,6 +24,8 @@ from .stencil import (  # noqa: F401
     stencil_matrix,
     laplace_2d,
     laplace_3d,
+    uniflow_2d,
+    bentpipe_2d,
     box_2d,
     star_3d,
     box_3d,

@@ -281,6 +281,17 @@ def laplace_3d(side: int) -> Problem:
     return stencil_matrix((side, side, side), offs, f"laplace3d_{side}")
 
 
+def uniflow_2d(side: int) -> Problem:
+    """UniFlow2D-like stand-in (Galeri's matrix is absent): 5-point upwind
+    convection-diffusion with a uniform diagonal wind, Peclet 100."""
+    return conv_diff_2d(side, 100.0, (1.0, 1.0), name=f"uniflow2d_{side}")
+
+
+def bentpipe_2d(side: int) -> Problem:
+    """BentPipe2D-like stand-in: convection at an angle, Peclet 50."""
+    return conv_diff_2d(side, 50.0, (0.8, -0.6), name=f"bentpipe2d_{side}")
+
+
 def box_2d(side: int) -> Problem:
     """9-point box stencil (Galeri Star2D / Cross-like 3x3 neighbourhood)."""
     offs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]

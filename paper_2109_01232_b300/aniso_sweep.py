@@ -1,11 +1,14 @@
 """The anisotropic 2D workload: inner precision x polynomial degree sweep (Section 5.4's
 experiment on this GPU).
 
-2000^2 anisotropic convection-diffusion (eps 1e-2, Pe 100, b = ones): GMRES-IR with FP32,
-FP16-storage and BF16-storage inner GMRES(50) and a right GMRES-polynomial preconditioner of
-degree 10, 25 and 40, and FP64 GMRES(50) with the same polynomials; each run's explicit
-relative residual and its error against an FP64 reference solution (FP64 GMRES with the
-degree-40 polynomial solved to 1e-11).  Each solve is capped at 20,000 iterations.
+2000^2 anisotropic convection-diffusion (eps 1e-2, Pe 100, b = ones): for polynomial
+degrees 10, 25 and 40, the three configurations of Section 5.4 -- FP64 GMRES(50) with the
+polynomial in FP64, FP64 GMRES(50) with the polynomial applied in FP32, GMRES-IR with an
+FP32 inner cycle (polynomial in FP32) -- and GMRES-IR with FP16 and BF16 storage.  Each
+run reports its explicit relative residual and its error against the exact solution that
+the oracle's sparse direct solve wrote to oracle/aniso<side>_reference.npy (checked
+against the SHA-256 in oracle/aniso<side>_reference.json; make it with
+`python -m oracle.record_aniso_reference`).  Each solve is capped at 20,000 iterations.
 
     python -m paper_2109_01232_b300.aniso_sweep [--side 2000]
 """
@@ -17,27 +20,40 @@ import sys
 
 import numpy as np
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
 
 
-def run(side: int = 2000, m: int = 50, rtol: float = 1e-10, max_iters: int = 20000, log=None):
+def reference_solution(side: int) -> np.ndarray:
+    """The exact solution recorded by the oracle's direct solve, verified by its hash."""
+    import hashlib
+    import json
+    stem = os.path.join(ROOT, "oracle", f"aniso{side}_reference")
+    if not (os.path.exists(stem + ".npy") and os.path.exists(stem + ".json")):
+        raise SystemExit(f"{stem}.npy is missing: run `python -m oracle.record_aniso_reference "
+                         f"--side {side}` first")
+    x = np.load(stem + ".npy")
+    if hashlib.sha256(x.tobytes()).hexdigest() != json.load(open(stem + ".json"))["sha256"]:
+        raise SystemExit(f"{stem}.npy does not match its recorded hash")
+    return x
+
+
+def run(side: int = 2000, m: int = 50, rtol: float = 1e-10, max_iters: int = 20000, log=None,
+        x_ref: np.ndarray | None = None):
+    """x_ref: the exact solution (default: the recorded one for this side)."""
     import torch
 
     import gen
     import paper_2109_01232_b300 as g
     p, b = gen.config_aniso_2d(side=side)
+    xr = torch.tensor(reference_solution(side) if x_ref is None else x_ref, device="cuda")
+    nref = float(torch.linalg.norm(xr))
     A = g.DeviceCSR.from_problem(p)
     bt = torch.tensor(b, device="cuda")
-    xr = torch.zeros_like(bt)
-    ref = g.gmres_solve(A, bt, xr, restart_m=m, rtol=1e-11, poly_degree=40, seed=7,
-                        max_iters=max_iters)
-    nref = float(torch.linalg.norm(xr))
-    rows = [dict(solver="FP64 GMRES (reference, tol 1e-11)", degree=40, status=ref.status_name,
-                 iters=ref.iters, ms=ref.t_solve_ms, relres=ref.relres, err=0.0)]
-    if log:
-        log(rows[-1])
+    rows = []
     for d in (10, 25, 40):
-        runs = [("FP64 GMRES", g.gmres_solve, {})] + [
+        runs = [("FP64 GMRES, FP64 polynomial", g.gmres_solve, {}),
+                ("FP64 GMRES, FP32 polynomial", g.gmres_solve, dict(poly_in_fp32=1))] + [
             (f"GMRES-IR {pr.upper()} inner", g.gmres_ir_solve, dict(inner_prec=pr))
             for pr in ("fp32", "fp16", "bf16")]
         for name, fn, kw in runs:
@@ -53,7 +69,7 @@ def run(side: int = 2000, m: int = 50, rtol: float = 1e-10, max_iters: int = 200
 
 def table(p, rows) -> str:
     out = [f"Matrix {p.name}: n = {p.n:,}, nnz = {len(p.vals):,}; m = 50, rtol 1e-10, x0 = 0, b = ones.", "",
-           "| solver | poly degree | status | iterations | solve ms | explicit relres | ||x - x_ref|| / ||x_ref|| |",
+           "| solver | poly degree | status | iterations | solve ms | explicit relres | ||x - x*|| / ||x*|| (x*: oracle's exact solve) |",
            "|---|---:|---|---:|---:|---:|---:|"]
     for r in rows:
         out.append(f"| {r['solver']} | {r['degree']} | {r['status']} | {r['iters']} | {r['ms']:.1f} | "

@@ -65,10 +65,13 @@ def _solve_time(g, torch, plan, bt, x, rtol, tol, max_iters):
     return (r.t_solve_ms if r.status == g.OK else np.inf), r.iters
 
 
-def sweep(descs, rtol: float = 1e-10, log=print, checkpoint: str | None = None):
-    """For each matrix descriptor (gen.selector_matrices): features, the default's time and
-    the device time (ms) of every (class, tolerance), inf for a failure or a timeout.  With
-    `checkpoint`, the matrices done so far are saved there after each one."""
+def sweep(descs, rtol: float = 1e-10, log=print, checkpoint: str | None = None,
+          tol_index=None, n_hi: float = 2e5):
+    """For each matrix descriptor (gen.selector_matrices with this n_hi): features, the
+    default's time and the device time (ms) of every (class, tolerance), inf for a failure or
+    a timeout.  tol_index (one tolerance index per class, e.g. a trained model's) restricts
+    each class to that tolerance (the others stay inf), a third of the runs for large
+    matrices.  With `checkpoint`, the matrices done so far are saved there after each one."""
     import torch
 
     import gen
@@ -110,6 +113,8 @@ def sweep(descs, rtol: float = 1e-10, log=print, checkpoint: str | None = None):
             per_it = rp_.t_solve_ms / max(rp_.iters, 1)
             cap = int(min(DEFAULT_CAP, max(m, 1.2 * TIMEOUT_FACTOR * t_ref / max(per_it, 1e-6)) + m))
             for it_, tol in enumerate(TOLS):
+                if tol_index is not None and it_ != int(tol_index[c]):
+                    continue
                 t, its = _solve_time(g, torch, plan, bt, x, rtol, tol, cap)
                 if t > TIMEOUT_FACTOR * t_ref:
                     t = np.inf
@@ -120,14 +125,74 @@ def sweep(descs, rtol: float = 1e-10, log=print, checkpoint: str | None = None):
             f"an={desc['anisotropy']:.3g} default {t0:.1f} ms ({it0} it), best "
             f"{np.min(T[k]):.1f} ms, {time.time() - t_start:.1f} s")
         if checkpoint:
-            save(checkpoint, _sweep_dict(F, T, It, T0, descs, k + 1))
-    return _sweep_dict(F, T, It, T0, descs, len(descs))
+            save(checkpoint, _sweep_dict(F, T, It, T0, descs, k + 1, n_hi))
+    return _sweep_dict(F, T, It, T0, descs, len(descs), n_hi)
 
 
-def _sweep_dict(F, T, It, T0, descs, done: int) -> dict:
+def _sweep_dict(F, T, It, T0, descs, done: int, n_hi: float) -> dict:
+    """desc_index / desc_n_hi identify each matrix: gen.selector_matrices(count > index,
+    n_hi=desc_n_hi)[desc_index]."""
     return dict(features=F[:done], times=T[:done], iters=It[:done], default_ms=T0[:done],
                 desc_index=np.array([d["index"] for d in descs[:done]]),
-                desc_seed=np.array([d["seed"] for d in descs[:done]]))
+                desc_seed=np.array([d["seed"] for d in descs[:done]]),
+                desc_n_hi=np.full(done, n_hi), desc_n=np.array([d["side"] ** d["dim"]
+                                                                for d in descs[:done]]))
+
+
+def descriptor(data: dict, k: int) -> dict:
+    """The corpus descriptor of matrix k of a sweep."""
+    import gen
+    idx = int(data["desc_index"][k])
+    n_hi = float(data["desc_n_hi"][k]) if "desc_n_hi" in data else float(data.get("n_hi", 2e5))
+    return gen.selector_matrices(count=idx + 1, n_hi=n_hi)[idx]
+
+
+def live_evaluate(data: dict, model: dict, idx, rtol: float = 1e-10, reps: int = 2,
+                  log=None) -> dict:
+    """Re-solve the matrices idx with the selector's choice (gmres_select_params through
+    Selector.choose, on the GPU-computed features) and with the default, from b = ones,
+    x0 = 0: device time of each (median of `reps` after a warm-up), status and relres."""
+    import torch
+
+    import gen
+    import paper_2109_01232_b300 as g
+    sel = g.Selector(model)
+    rows = []
+    for k in idx:
+        desc = descriptor(data, k)
+        p = gen.build_selector_matrix(desc)
+        A = g.DeviceCSR.from_problem(p)
+        bt = torch.ones(p.n, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(bt)
+        ps, cls, conf = sel.choose(A)
+        chosen = dict(restart_m=int(ps.restart_m), inner_prec=int(ps.inner_prec),
+                      poly_degree=int(ps.poly_degree), inner_rtol=float(ps.inner_rtol))
+        out = {}
+        for name, prm in (("default", dict(restart_m=DEFAULT["m"], inner_prec=DEFAULT["prec"],
+                                           poly_degree=DEFAULT["degree"],
+                                           inner_rtol=DEFAULT["inner_rtol"])),
+                          ("selected", chosen)):
+            plan = g.Plan(A, "ir", rtol=rtol, max_iters=DEFAULT_CAP, seed=desc["seed"], **prm)
+            ts, r = [], None
+            for _ in range(reps + 1):
+                x.zero_()
+                r = plan.solve(bt, x)
+                ts.append(r.t_solve_ms)
+            plan.close()
+            out[name] = dict(ms=float(np.median(ts[1:])), status=r.status_name, iters=r.iters,
+                             relres=r.relres)
+        row = dict(index=int(k), n=p.n, chosen=chosen, cls=cls, confidence=conf, **out)
+        rows.append(row)
+        if log:
+            log(row)
+    ok_def = [r for r in rows if r["default"]["status"] == "OK"]
+    ratio = [r["selected"]["ms"] / r["default"]["ms"] for r in ok_def
+             if r["selected"]["status"] == "OK"]
+    lost = sum(1 for r in ok_def if r["selected"]["status"] != "OK")
+    return dict(rows=rows, geomean_ratio=float(np.exp(np.mean(np.log(ratio)))) if ratio else None,
+                lost_convergence=lost, n=len(rows),
+                converged_default=len(ok_def),
+                converged_selected=sum(1 for r in rows if r["selected"]["status"] == "OK"))
 
 
 def split(n: int, held_out: int, seed: int = 4999):
@@ -220,10 +285,19 @@ def main(argv=None):
     s1.add_argument("--n-hi", type=float, default=2e5)
     s1.add_argument("--first", type=int, default=0, help="sweep matrices [first, last) only")
     s1.add_argument("--last", type=int, default=None)
+    s1.add_argument("--n-range", type=float, nargs=2, default=None,
+                    help="only the matrices with lo <= N <= hi")
+    s1.add_argument("--max", type=int, default=None, help="at most this many matrices")
+    s1.add_argument("--tols-from", default=None,
+                    help="a model whose per-class tolerance each class is restricted to")
     s1.add_argument("--out", default=SWEEP_PATH)
     s3 = sub.add_parser("merge")
     s3.add_argument("parts", nargs="+")
     s3.add_argument("--out", default=SWEEP_PATH)
+    s4 = sub.add_parser("live")
+    s4.add_argument("--sweep", default=SWEEP_PATH)
+    s4.add_argument("--model", default=MODEL_PATH)
+    s4.add_argument("--n-max", type=float, default=2e6)
     s2 = sub.add_parser("fit")
     s2.add_argument("--sweep", default=SWEEP_PATH)
     s2.add_argument("--held-out", type=float, default=0.2)
@@ -231,16 +305,31 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.cmd == "sweep":
         descs = gen.selector_matrices(count=a.count, n_hi=a.n_hi)[a.first:a.last]
-        data = sweep(descs, checkpoint=a.out)
-        data["n_hi"] = np.float64(a.n_hi)
+        if a.n_range:
+            descs = [d for d in descs if a.n_range[0] <= d["side"] ** d["dim"] <= a.n_range[1]]
+        descs = descs[:a.max]
+        tol_index = load(a.tols_from)["tol_index"] if a.tols_from else None
+        data = sweep(descs, checkpoint=a.out, tol_index=tol_index, n_hi=a.n_hi)
         save(a.out, data)
     elif a.cmd == "merge":
         parts = [load(q) for q in a.parts]
-        data = {k: np.concatenate([q[k] for q in parts]) for k in parts[0] if k != "n_hi"}
-        order = np.argsort(data["desc_index"], kind="stable")
+        for q in parts:  # sweeps written before desc_n_hi existed carry one n_hi for all
+            if "desc_n_hi" not in q:
+                q["desc_n_hi"] = np.full(len(q["default_ms"]), float(q.get("n_hi", 2e5)))
+            if "desc_n" not in q:
+                d0 = gen.selector_matrices(count=int(q["desc_index"].max()) + 1,
+                                           n_hi=float(q["desc_n_hi"][0]))
+                q["desc_n"] = np.array([d0[i]["side"] ** d0[i]["dim"] for i in q["desc_index"]])
+        keys = [k for k in parts[0] if k != "n_hi"]
+        data = {k: np.concatenate([q[k] for q in parts]) for k in keys}
+        order = np.lexsort((data["desc_index"], data["desc_n_hi"]))
         data = {k: v[order] for k, v in data.items()}
-        data["n_hi"] = parts[0]["n_hi"]
         save(a.out, data)
+    elif a.cmd == "live":
+        data, model = load(a.sweep), load(a.model)
+        idx = [int(k) for k in model["held_out"] if data["desc_n"][k] <= a.n_max]
+        res = live_evaluate(data, model, idx, log=print)
+        print({k: v for k, v in res.items() if k != "rows"})
     else:
         data = load(a.sweep)
         n = len(data["default_ms"])

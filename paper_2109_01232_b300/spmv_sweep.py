@@ -23,10 +23,10 @@ CASES = [("laplace_2d", 1500), ("laplace_2d", 2500), ("laplace_3d", 100), ("lapl
 
 def build(kind: str, side: int):
     import gen
-    if kind == "uniflow_2d":  # UniFlow2D-like: uniform wind, Peclet 100
-        return gen.conv_diff_2d(side, 100.0, (1.0, 1.0), name=f"uniflow2d_{side}")
-    if kind == "bentpipe_2d":  # BentPipe2D-like stand-in: convection at an angle, Peclet 50
-        return gen.conv_diff_2d(side, 50.0, (0.8, -0.6), name=f"bentpipe2d_{side}")
+    if kind == "uniflow_2d":
+        return gen.uniflow_2d(side)
+    if kind == "bentpipe_2d":
+        return gen.bentpipe_2d(side)
     return getattr(gen, kind)(side)
 
 

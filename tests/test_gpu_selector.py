@@ -113,3 +113,23 @@ def test_trained_selector_gains_on_held_out(g):
     X = (data["features"][te] - model["feat_mean"]) * model["feat_scale"]
     Po, _ = osel.forward(model["params"].astype(np.float64), X.astype(np.float64))
     assert np.array_equal(Po.argmax(axis=1), res["chosen"])
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(__file__), "..",
+                                                    "paper_2109_01232_b300", "selector_model.npz")),
+                    reason="no trained selector model committed")
+def test_selector_choice_beats_default_on_fresh_solves(g):
+    """Held-out matrices (up to 4e5 rows) solved again on the GPU, from b = ones, with the
+    selector's choice (gmres_select_params on GPU-computed features) and with the fixed
+    default: the chosen configurations are faster (geometric mean of the device times) and
+    every solve the default converges on still converges."""
+    from paper_2109_01232_b300 import selector as ps
+    model, data = ps.load(ps.MODEL_PATH), ps.load(ps.SWEEP_PATH)
+    idx = [int(k) for k in model["held_out"]
+           if ps.descriptor(data, k)["side"] ** ps.descriptor(data, k)["dim"] <= 4e5][:16]
+    assert len(idx) >= 10
+    res = ps.live_evaluate(data, model, idx, reps=2)
+    assert res["n"] == len(idx)
+    assert res["lost_convergence"] == 0
+    assert res["converged_selected"] >= res["converged_default"]
+    assert res["geomean_ratio"] < 1.0, res
