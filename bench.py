@@ -510,8 +510,9 @@ def cpu_baseline(p, b) -> dict:
     rec_ir, rec_64 = _recorded("pe10"), _recorded("pe10_fp64")
     t_ir = oracle_cycle_s(p, b, fp64=False)
     t_64 = oracle_cycle_s(p, b, fp64=True)
-    n_ir = int(rec_ir["outer"]) if rec_ir else 14
-    n_64 = int(rec_64["outer"]) if rec_64 else None
+    # cycle-equivalents of the oracle's own full solves (FP64's last cycle is partial)
+    n_ir = int(rec_ir["iters"]) / M if rec_ir else 14.0
+    n_64 = int(rec_64["iters"]) / M if rec_64 else None
     small = small_case_oracle()
     return {"value": t_ir * n_ir, "unit": "s", "cores": threads_used(), "kind": "oracle",
             "fp64_gmres_s": t_64 * n_64 if n_64 else None,
@@ -519,9 +520,9 @@ def cpu_baseline(p, b) -> dict:
             "small_64x64": small,
             "sample": f"oracle.gmres_ir (numpy, FP32-emulated inner GMRES(50)) on the Pe 10 "
                       f"100^3 instance: one whole refinement step (residual, 50 Arnoldi steps, "
-                      f"least squares, update, residual) took {t_ir:.2f} s, x {n_ir} steps of "
+                      f"least squares, update, residual) took {t_ir:.2f} s, x {n_ir:g} cycles of "
                       f"the oracle's own full solve; FP64 GMRES(50): one cycle {t_64:.2f} s x "
-                      f"{n_64} cycles; 64x64 case: full solves.  The sparse products run on one "
+                      f"{n_64:g} cycle-equivalents; 64x64 case: full solves.  The sparse products run on one "
                       f"thread (numpy), the dense basis products on `cores` BLAS threads"}
 
 
