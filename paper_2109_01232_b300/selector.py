@@ -212,16 +212,19 @@ def fit(data: dict, train_idx, epochs: int = 1000, lr: float = 3e-3, seed: int =
     import gen
     import paper_2109_01232_b300 as g
     T, T0, F = data["times"][train_idx], data["default_ms"][train_idx], data["features"][train_idx]
+    # each class keeps the tolerance with the smallest geometric-mean time ratio to the
+    # default, over the training matrices on which the default converges
     ok = np.isfinite(T0)
-    T, T0, F = T[ok], T0[ok], F[ok]
-    # each class keeps the tolerance with the smallest geometric-mean time ratio
     tol_idx = np.zeros(N_CLASSES, int)
     for c in range(N_CLASSES):
-        gm = [np.exp(np.mean(np.log(_ratio(T[:, c, t], T0)))) for t in range(len(TOLS))]
+        gm = [np.exp(np.mean(np.log(_ratio(T[ok, c, t], T0[ok])))) for t in range(len(TOLS))]
         tol_idx[c] = int(np.argmin(gm))
+    # labels: the fastest class on every training matrix that some class solves (also where
+    # the default does not converge)
     Tc = np.stack([T[:, c, tol_idx[c]] for c in range(N_CLASSES)], axis=1)
+    solved = np.isfinite(Tc).any(axis=1)
+    T, T0, F, Tc = T[solved], T0[solved], F[solved], Tc[solved]
     labels = np.argmin(np.where(np.isfinite(Tc), Tc, np.inf), axis=1)
-    labels[~np.isfinite(Tc).any(axis=1)] = DEFAULT_CLASS
     mean = F.mean(axis=0)
     std = F.std(axis=0)
     scale = np.where(std > 1e-6, 1.0 / np.maximum(std, 1e-6), 0.0).astype(np.float32)
