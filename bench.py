@@ -275,6 +275,35 @@ def run_batched(g, torch, peak):
                     "frac": nbytes / t / 1e9 / peak}}
 
 
+# ---------------------------------------------------------- small case ----
+def run_small_case(g, torch, reps: int = 20) -> dict:
+    """The plain-method small case (2D 64 x 64, Pe 10, b = A x_true, x0 = 0, rtol 1e-10):
+    FP64 GMRES(50) and GMRES-IR (FP32 inner GMRES(50), inner tolerance 1e-4) through a
+    reused plan, median device time of `reps` solves after a warm-up.  Everything fits in
+    L2, so this case is latency-bound: time and solves/s, no HBM fraction."""
+    import gen
+    p, b, x_true = gen.config_small_2d()
+    A = g.DeviceCSR.from_problem(p)
+    bt = torch.tensor(b, device="cuda")
+    x = torch.zeros_like(bt)
+    out = {"workload": "2D 5-point convection-diffusion 64x64 (n=4096), Pe 10, b = A x_true, "
+                       "x0 = 0, rtol 1e-10; reused plan, median of %d solves" % reps}
+    for name, kind, kw in (("fp64_gmres", "gmres", {}), ("gmres_ir", "ir", dict(inner_rtol=1e-4))):
+        plan = g.Plan(A, kind, restart_m=M, rtol=RTOL, **kw)
+        ts, r = [], None
+        for _ in range(reps + 1):
+            x.zero_()
+            r = plan.solve(bt, x)
+            ts.append(r.t_solve_ms)
+        plan.close()
+        err = float(np.linalg.norm(x.cpu().numpy() - x_true) / np.linalg.norm(x_true))
+        t = statistics.median(ts[1:])
+        out[name] = {"ms": t, "solves_per_s": 1e3 / t, "iters": r.iters, "status": r.status_name,
+                     "relres": r.relres, "x_err_vs_x_true": err}
+    out["speedup_ir_vs_fp64"] = out["fp64_gmres"]["ms"] / out["gmres_ir"]["ms"]
+    return out
+
+
 # ------------------------------------------------------------- multi-rank ----
 def max_over_ranks(value: float, dist=None) -> float:
     """The largest `value` over the ranks of the default process group (replicas: every
@@ -415,6 +444,7 @@ def run_ours(args, rank, world, local_rank):
         h2d = 4 * (p.n + 1) + 12 * p.nnz + 16 * p.n
         cpu = None if args.no_cpu_baseline else cpu_baseline(it["p"], it["b"])
         batched = None if args.no_batched else run_batched(g, torch, peak)
+        small = run_small_case(g, torch)
         out = {
             "metric": METRIC, "value": per_solve_s, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -441,6 +471,7 @@ def run_ours(args, rank, world, local_rank):
             "kernel_speedup_vs_fp64": kernel_speedup,
             "cpu_baseline": cpu,
             "batched": batched,
+            "small_case": small,
             "e2e": {"value": statistics.median(e2e), "unit": "s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8 * p.n,
                     "what": "gmres_ir_solve_host on the Pe 10 instance from pinned host memory: "
@@ -481,23 +512,44 @@ def oracle_cycle_s(p, b, fp64: bool) -> float:
     return _time(lambda: oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", max_iters=M))
 
 
+SMALL_CASE_CODE = """
+import json, statistics, sys, time
+sys.path.insert(0, {root!r})
+import gen, oracle
+p, b, _ = gen.config_small_2d()
+runs = {{"fp64_gmres": lambda: oracle.gmres(p, b, m={m}, rtol={rtol}),
+        "gmres_ir": lambda: oracle.gmres_ir(p, b, m={m}, rtol={rtol}, inner="fp32", inner_rtol=1e-4)}}
+out = {{}}
+for name, fn in runs.items():
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        info = fn()[1]
+        ts.append(time.perf_counter() - t0)
+    out[name] = {{"s_median_of_3": statistics.median(ts), "iters": int(info.iters)}}
+print(json.dumps(out))
+"""
+
+
 def small_case_oracle(one_thread: bool = True) -> dict:
     """The plain-method small case (2D 64 x 64, Pe 10, b = A x_true): oracle FP64 GMRES(50)
     and GMRES-IR (FP32 inner GMRES(50), inner tolerance 1e-4) solved to 1e-10, median of 3
-    full solves on all BLAS threads and on one."""
-    import gen
-    import oracle
-    from threadpoolctl import threadpool_limits
-    p, b, _ = gen.config_small_2d()
-    runs = {"fp64_gmres": lambda: oracle.gmres(p, b, m=M, rtol=RTOL),
-            "gmres_ir": lambda: oracle.gmres_ir(p, b, m=M, rtol=RTOL, inner="fp32", inner_rtol=1e-4)}
-    out = {}
-    for name, fn in runs.items():
-        out[name] = {"s_median_of_3": statistics.median(_time(fn) for _ in range(3)),
-                     "iters": int(fn()[1].iters)}
-        if one_thread:
-            with threadpool_limits(1):
-                out[name]["s_1_thread"] = statistics.median(_time(fn) for _ in range(3))
+    full solves, in a child process with the default BLAS threads and in one with a single
+    thread (OPENBLAS/OMP/MKL_NUM_THREADS=1)."""
+    code = SMALL_CASE_CODE.format(root=ROOT, m=M, rtol=RTOL)
+    res = {}
+    for label, extra in (("all", {}), ("one", {"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1",
+                                               "MKL_NUM_THREADS": "1"})):
+        if label == "one" and not one_thread:
+            continue
+        env = dict(os.environ, **extra)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           check=True)
+        res[label] = json.loads(r.stdout.strip().splitlines()[-1])
+    out = res["all"]
+    if "one" in res:
+        for name in out:
+            out[name]["s_1_thread"] = res["one"][name]["s_median_of_3"]
     return out
 
 
@@ -527,12 +579,19 @@ def cpu_baseline(p, b) -> dict:
 
 
 def threads_used() -> int:
+    """BLAS threads of this process: threadpoolctl's count where it is installed, else the
+    OPENBLAS/OMP thread variable, else every core (OpenBLAS's default)."""
     try:
         from threadpoolctl import threadpool_info
         n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
-        return int(max(n)) if n else 1
+        if n:
+            return int(max(n))
     except Exception:
-        return os.cpu_count() or 1
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count() or 1
 
 
 # --------------------------------------------------------- reference arm ----
