@@ -23,10 +23,13 @@ constexpr int TILE_MAX = 4096;    // largest SpMV row tile; every buffer's leadi
 // products (its warp tile is VT slices of 32 rows: 128 rows in every low precision; with
 // 256-row tiles in FP16/BF16 a CTA had fewer tiles than warps on 10^6 rows).
 template <int P> struct Tr;
-template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2, VT = 2; };
-template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4; };
-template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4; };
-template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4; };
+// V_EF: the SpMV kernel reads the old basis columns with the half-evict-first L2 policy
+// (FP64/FP32) or plainly (FP16/BF16: their basis is small enough that keeping all of it in
+// L2 for the CGS kernels measured faster).
+template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2, VT = 2; static constexpr bool V_EF = true; };
+template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4; static constexpr bool V_EF = true; };
+template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4; static constexpr bool V_EF = false; };
+template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4; static constexpr bool V_EF = false; };
 
 // storage -> working type
 __device__ __forceinline__ double to_w(double v) { return v; }
@@ -101,9 +104,13 @@ __device__ __forceinline__ void ldv_stream(const T* __restrict__ p, T (&o)[N]) {
 // data needs the cache (the basis V streams through L2 once per pass, and marking it
 // keeps the matrix and the work vectors resident).  Only for memory that no thread
 // writes during the kernel: the asm is not ordered against other memory operations.
+// Half of the lines get the evict-first policy, the others keep the normal one: of the
+// fractions measured in the SpMV's dot products on the 100^3 workload (FP32: 0, 0.25, 0.5,
+// 0.75, 1), 0.5 gave the shortest solves -- the next kernel still finds part of the basis in
+// L2 while the gathered vector stays resident.
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long pol;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 0.5;" : "=l"(pol));
   return pol;
 }
 template <class T, int N>

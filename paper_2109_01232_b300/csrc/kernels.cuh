@@ -121,7 +121,9 @@ __device__ __forceinline__ bool arrive_last(unsigned int* ticket, int* s_last) {
 // gather).  Measured on a B300 it shortens the FP16 SpMV by 9% and lengthens the FP32 one
 // by 2% (its extra registers), so FP32/FP64 keep the plain loop.  Products and their order
 // are the same either way.
-template <int EB, class AT, int R>
+// MS: the matrix is read once by this kernel; load it evict-first (ld.cs) so that it does not
+// push other data out of L2.
+template <int EB, class AT, int R, bool MS = false>
 __device__ __forceinline__ void sell_load(const int2 (&mt)[R], int e0, const int* __restrict__ sc,
                                           const AT* __restrict__ sv, int lane, int (&ci)[EB][R],
                                           AT (&va)[EB][R]) {
@@ -131,8 +133,13 @@ __device__ __forceinline__ void sell_load(const int2 (&mt)[R], int e0, const int
     for (int k = 0; k < R; ++k) {
       const bool ok = e0 + eb < mt[k].y;
       const int idx = mt[k].x + (e0 + eb) * 32 + lane;
-      ci[eb][k] = ok ? sc[idx] : -1;
-      va[eb][k] = ok ? sv[idx] : AT(0);
+      if constexpr (MS) {
+        ci[eb][k] = ok ? __ldcs(sc + idx) : -1;
+        va[eb][k] = ok ? __ldcs(sv + idx) : AT(0);
+      } else {
+        ci[eb][k] = ok ? sc[idx] : -1;
+        va[eb][k] = ok ? sv[idx] : AT(0);
+      }
     }
   }
 }
@@ -158,20 +165,20 @@ __device__ __forceinline__ void sell_gathers(const int (&ci)[EB][R], const XF& x
   }
 }
 
-template <int EB, class AT, class W, int R, class XF>
+template <int EB, bool MS = false, class AT, class W, int R, class XF>
 __device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, const int* __restrict__ sc,
                                                 const AT* __restrict__ sv, int lane, const XF& xval,
                                                 W (&acc)[R]) {
   if constexpr (sizeof(AT) == 2) {
     int ci[EB][R];
     AT va[EB][R];
-    sell_load<EB, AT, R>(mt, 0, sc, sv, lane, ci, va);
+    sell_load<EB, AT, R, MS>(mt, 0, sc, sv, lane, ci, va);
     for (int e0 = 0; e0 < maxw; e0 += EB) {
       W xv[EB][R];
       sell_gathers<EB, AT, W, R>(ci, xval, xv);
       int cn[EB][R];
       AT vn[EB][R];
-      sell_load<EB, AT, R>(mt, e0 + EB, sc, sv, lane, cn, vn);  // none past maxw
+      sell_load<EB, AT, R, MS>(mt, e0 + EB, sc, sv, lane, cn, vn);  // none past maxw
       sell_products<EB, AT, W, R, XF>(ci, va, xv, acc);
 #pragma unroll
       for (int eb = 0; eb < EB; ++eb) {
@@ -186,7 +193,7 @@ __device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, c
     for (int e0 = 0; e0 < maxw; e0 += EB) {
       int ci[EB][R];
       AT va[EB][R];
-      sell_load<EB, AT, R>(mt, e0, sc, sv, lane, ci, va);
+      sell_load<EB, AT, R, MS>(mt, e0, sc, sv, lane, ci, va);
       W xv[EB][R];
       sell_gathers<EB, AT, W, R>(ci, xval, xv);
       sell_products<EB, AT, W, R, XF>(ci, va, xv, acc);
@@ -508,10 +515,11 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
 // once j is large, and LRU keeps what a kernel touched last.  Consecutive step kernels
 // therefore walk their CTA's rows in opposite directions (k_spmv_sell forward for even j,
 // k_cgs_u1 the other way, k_cgs_u2 like k_spmv_sell), so each starts on the rows whose
-// basis entries the previous kernel left in L2.  The SpMV's dot products read the old
-// columns evict-first (ldv_evict_first), which keeps the matrix and the vectors that the
-// CGS kernels read next; measured on a B300, evict-first loads in the CGS kernels
-// themselves cost more than they saved.
+// basis entries the previous kernel left in L2.  The SpMV streams the matrix evict-first
+// (it is read once per step) and reads the old basis columns with half of them evict-first
+// in FP64/FP32 and plainly in FP16/BF16 (Tr::V_EF), so the CGS kernels that follow find
+// much of the basis in L2 while the gathered vector stays resident; measured on a B300,
+// evict-first loads in the CGS kernels themselves cost more than they saved.
 // ===========================================================================
 
 // Partial-sum buffers of one Arnoldi step (working type, column-major: column c of a
@@ -872,7 +880,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     W a[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) a[q] = W(0);
-    sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, a);
+    // The matrix is read once per step and evicted by the CGS kernels' streams anyway: loaded
+    // evict-first, it leaves L2 to the basis the next kernels read (with a polynomial the
+    // matrix is re-read d times per step and keeps the normal policy).
+    sell_accumulate<2, !PLAIN>(mt, maxw, sc, sv, lane, xval, a);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       const int row = r0 + 32 * q + lane;
@@ -888,8 +899,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     W nrm = W(0);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
-    // columns 0..j-1 are read-only here (evict-first); column j was just stored by the warp
-    dots_to_acc<true, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j, wv, acc);
+    // columns 0..j-1 are read-only here (half evict-first in FP64/FP32, see Tr::V_EF);
+    // column j was just stored by the warp
+    dots_to_acc<Tr<P>::V_EF, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j, wv, acc);
     dots_to_acc<false, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc, j);
     nrm = warp_sum(nrm);
     if (lane == 0) acc[j + 1] += nrm;
