@@ -278,6 +278,13 @@ int gmres_plan_poly_roots(gmres_plan plan, double* roots_re, double* roots_im, i
  * cycle did not reach. */
 int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0, double* ms_out,
                              void* stream);
+/* The same breakdown measured as a solve runs the cycle: one restart cycle captured as
+ * a CUDA graph with an event-record node (cudaEventRecordExternal) before every kernel
+ * and after the last, launched once; ms_out[i] = time between the events around kernel
+ * i (same layout and -1 convention as gmres_plan_profile_cycle).  Instantiates a
+ * graph per call (not for use inside a solve loop); synchronises the stream. */
+int gmres_plan_profile_cycle_graph(gmres_plan plan, const double* b, const double* x0,
+                                   double* ms_out, void* stream);
 
 /* Plan geometry: info_out (HOST, 8 int64) = n, nnz, leading dimension ld,
  * m, storage precision, grid of the SpMV kernel, grid of the CGS kernels,

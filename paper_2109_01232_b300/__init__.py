@@ -101,6 +101,7 @@ _SIGNATURES = {
                                         ctypes.POINTER(_I32), _P]),
     "gmres_splitmix64_fill": (ctypes.c_int, [_P, _I64, _U64, _P]),
     "gmres_plan_profile_cycle": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gmres_plan_profile_cycle_graph": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gmres_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
@@ -390,14 +391,15 @@ class Plan:
         keys = ["n", "nnz", "ld", "m", "prec", "grid_spmv", "grid_vec", "grid_res"]
         return dict(zip(keys, map(int, out)))
 
-    def profile_cycle(self, b, x0, stream=None) -> np.ndarray:
-        """Per-launch device times (ms) of one cycle run kernel by kernel, shape (m+1, 3):
-        row j = (SpMV, first CGS update, second CGS update) of step j, last row = (least
-        squares, x update, residual); -1 where the cycle ended earlier."""
+    def profile_cycle(self, b, x0, stream=None, graph: bool = False) -> np.ndarray:
+        """Per-launch device times (ms) of one cycle, shape (m+1, 3): row j = (SpMV, first CGS
+        update, second CGS update) of step j, last row = (least squares, x update, residual);
+        -1 where the cycle ended earlier.  graph=False: kernels launched one by one with events
+        around each; graph=True: event-record nodes inside a captured graph of the cycle."""
         m = int(self.params.restart_m)
         out = np.zeros(3 * m + 3, dtype=np.float64)
-        _check(lib().gmres_plan_profile_cycle(self.handle, _ptr(b), _ptr(x0), out.ctypes.data,
-                                              _stream(stream)), "profile_cycle")
+        fn = lib().gmres_plan_profile_cycle_graph if graph else lib().gmres_plan_profile_cycle
+        _check(fn(self.handle, _ptr(b), _ptr(x0), out.ctypes.data, _stream(stream)), "profile_cycle")
         return out.reshape(m + 1, 3)
 
     def close(self):

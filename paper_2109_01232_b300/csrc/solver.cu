@@ -996,6 +996,72 @@ int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_o
   return err;
 }
 
+// The same cycle as the plan's graph, captured with an event-record node before every
+// kernel and after the last (cudaEventRecordExternal), and launched once: ms_out[i] is the
+// time between the events around kernel i as it runs inside a graph, the way a solve runs
+// it (layout as plan_profile_cycle; -1 for the steps the cycle did not reach, whose kernels
+// returned at once).  Costs one graph instantiation per call.
+int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double* ms_out,
+                             cudaStream_t s) {
+  const int m = pl.m, nslots = 3 * m + 3;
+  init_state(pl, *pl.h_st);
+  CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  if (int e = load_rhs(pl, b, x0, s)) return e;
+  launch_residual(pl, 1, s);
+  CK(cudaStreamSynchronize(s));
+  std::vector<cudaEvent_t> ev((size_t)nslots + 1, nullptr);
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int err = GMRES_OK;
+  auto done = [&](int e) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+    return e;
+  };
+  for (auto& x : ev)
+    if ((err = CUDA_STATUS(cudaEventCreate(&x)))) return done(err);
+  if ((err = CUDA_STATUS(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))) return done(err);
+  if ((err = CUDA_STATUS(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))))
+    return done(err);
+  dispatch(pl.prec, [&](auto PP) -> int {
+    constexpr int P = decltype(PP)::value;
+    for (int j = 0; j < m; ++j)
+      for (int w = 0; w < 3; ++w) {
+        cudaEventRecordWithFlags(ev[3 * j + w], cs, cudaEventRecordExternal);
+        launch_step_kernel<P>(pl, j, w, cs);
+      }
+    for (int w = 0; w < 3; ++w) {
+      cudaEventRecordWithFlags(ev[3 * m + w], cs, cudaEventRecordExternal);
+      launch_tail_kernel<P>(pl, w, cs);
+    }
+    cudaEventRecordWithFlags(ev[nslots], cs, cudaEventRecordExternal);
+    return 0;
+  });
+  if ((err = CUDA_STATUS(cudaStreamEndCapture(cs, &graph)))) return done(err);
+  if ((err = CUDA_STATUS(cudaGraphInstantiate(&exec, graph, 0)))) return done(err);
+  if ((err = CUDA_STATUS(cudaGraphLaunch(exec, s)))) return done(err);
+  if ((err = CUDA_STATUS(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s))))
+    return done(err);
+  if ((err = CUDA_STATUS(cudaStreamSynchronize(s)))) return done(err);
+  // Arnoldi steps the cycle took (the solve's step count starts at zero in init_state;
+  // st->k is already reset for the next cycle by the residual kernel)
+  const long long steps = pl.h_st->iters;
+  for (int i = 0; i < nslots; ++i) {
+    const bool ran = i >= 3 * m || i / 3 < steps;
+    float ms = -1.f;
+    if (ran && cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    ms_out[i] = ran ? (double)ms : -1.0;
+  }
+  return done(GMRES_OK);
+}
+
 }  // namespace gm
 
 using gm::Plan;
@@ -1116,6 +1182,12 @@ int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0,
                              void* stream) {
   if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
   return gm::plan_profile_cycle(*plan->pl, b, x0, ms_out, (cudaStream_t)stream);
+}
+
+int gmres_plan_profile_cycle_graph(gmres_plan plan, const double* b, const double* x0,
+                                   double* ms_out, void* stream) {
+  if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
+  return gm::plan_profile_cycle_graph(*plan->pl, b, x0, ms_out, (cudaStream_t)stream);
 }
 
 int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream) {

@@ -344,3 +344,29 @@ def test_resume_from_a_checkpoint_equals_one_solve(g, torch, prec):
     assert first.outer + rest.outer == one.outer
     np.testing.assert_allclose(x2.cpu().numpy(), x1.cpu().numpy(), rtol=0, atol=1e-14 * float(
         torch.abs(x1).max()))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_profile_cycle_times_every_kernel_of_one_cycle(g, torch, graph):
+    """The per-kernel profile of one restart cycle (kernel by kernel, or inside a captured
+    graph with event-record nodes): every kernel of the steps the cycle took has a positive
+    time, the steps it did not reach are -1, and the cycle computes what a solve computes
+    (the next profile of the same plan gives the same step count)."""
+    p, b, _ = gen.config_small_2d(48)
+    A = g.DeviceCSR.from_problem(p)
+    bt, x0 = _dev(torch, b, np.zeros(p.n))
+    for m, inner_rtol in ((20, 0.0), (40, 1e-2)):  # the second cycle ends early
+        plan = g.Plan(A, "ir", restart_m=m, inner_rtol=inner_rtol)
+        ms = plan.profile_cycle(bt, x0, graph=graph)
+        assert ms.shape == (m + 1, 3)
+        ran = ms[:-1, 0] >= 0
+        k = int(ran.sum())
+        assert k >= 1 and ran[:k].all() and not ran[k:].any()
+        assert (ms[:k] > 0).all() and (ms[:-1][~ran] == -1).all() and (ms[-1] > 0).all()
+        if inner_rtol == 0.0:
+            assert k == m
+        else:
+            assert k < m
+        ms2 = plan.profile_cycle(bt, x0, graph=graph)
+        assert int((ms2[:-1, 0] >= 0).sum()) == k
+        plan.close()
