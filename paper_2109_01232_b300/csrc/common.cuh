@@ -184,6 +184,7 @@ struct DevState {
   double u_work;     // unit roundoff of the working precision
   double best_rel;   // IR: smallest explicit relative residual so far
   int stall;         // IR: refinement steps since best_rel last dropped by 0.1%
+  int stream_matrix; // 1: the preconditioned path's SpMVs load the copy of A evict-first
   unsigned int ticket[4];
 };
 

@@ -165,10 +165,11 @@ __device__ __forceinline__ void sell_gathers(const int (&ci)[EB][R], const XF& x
   }
 }
 
-template <int EB, bool MS = false, class AT, class W, int R, class XF>
-__device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, const int* __restrict__ sc,
-                                                const AT* __restrict__ sv, int lane, const XF& xval,
-                                                W (&acc)[R]) {
+template <int EB, bool MS, class AT, class W, int R, class XF>
+__device__ __forceinline__ void sell_accumulate_ms(const int2 (&mt)[R], int maxw,
+                                                   const int* __restrict__ sc,
+                                                   const AT* __restrict__ sv, int lane,
+                                                   const XF& xval, W (&acc)[R]) {
   if constexpr (sizeof(AT) == 2) {
     int ci[EB][R];
     AT va[EB][R];
@@ -201,10 +202,19 @@ __device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, c
   }
 }
 
+// ms: load the matrix evict-first (see sell_load); chosen once per call.
+template <int EB, class AT, class W, int R, class XF>
+__device__ __forceinline__ void sell_accumulate(const int2 (&mt)[R], int maxw, const int* __restrict__ sc,
+                                                const AT* __restrict__ sv, int lane, const XF& xval,
+                                                W (&acc)[R], bool ms = false) {
+  if (ms) sell_accumulate_ms<EB, true>(mt, maxw, sc, sv, lane, xval, acc);
+  else sell_accumulate_ms<EB, false>(mt, maxw, sc, sv, lane, xval, acc);
+}
+
 template <class AT, class W, int RPT, class XF>
 __device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const int* __restrict__ sc,
                                           const AT* __restrict__ sv, int nslices, int r0,
-                                          const XF& xval, W (&acc)[RPT]) {
+                                          const XF& xval, W (&acc)[RPT], bool ms = false) {
   const int lane = threadIdx.x & 31;
   const int s0 = (r0 >> 5) + (threadIdx.x >> 5);
   int2 mt[RPT];
@@ -216,7 +226,7 @@ __device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const i
     maxw = max(maxw, mt[k].y);
     acc[k] = W(0);
   }
-  sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, acc);
+  sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, acc, ms);
 }
 
 // Sum of the G per-CTA partials p[0..G) by one warp, four independent load streams per
@@ -847,6 +857,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
   }
   for (int c = lane; c < ncol; c += 32) acc[c] = W(0);
   __syncwarp();
+  const bool ms = PLAIN ? st->stream_matrix != 0 : true;
 
   const SrcT f = (SrcT)(v_scale * sigma);
   const W row_scale = (W)row_scale_d;
@@ -881,9 +892,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
 #pragma unroll
     for (int q = 0; q < VEC; ++q) a[q] = W(0);
     // The matrix is read once per step and evicted by the CGS kernels' streams anyway: loaded
-    // evict-first, it leaves L2 to the basis the next kernels read (with a polynomial the
-    // matrix is re-read d times per step and keeps the normal policy).
-    sell_accumulate<2, !PLAIN>(mt, maxw, sc, sv, lane, xval, a);
+    // evict-first, it leaves L2 to the basis the next kernels read.  After a preconditioner
+    // (PLAIN) the plan decides (DevState::stream_matrix): a polynomial re-reads the matrix d
+    // times per step, which pays only while it stays in L2.
+    sell_accumulate<2>(mt, maxw, sc, sv, lane, xval, a, ms);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       const int row = r0 + 32 * q + lane;

@@ -92,11 +92,12 @@ __global__ void __launch_bounds__(NT, 2) k_poly_spmv(
   const W as = (W)a_scale, c1 = (W)c1d, c2 = (W)c2d;
   const W* gsrc = KIND == POLY_PAIR_B ? tin : prod;
   auto xval = [&](int c) -> W { return gsrc[c]; };
+  const bool ms = st->stream_matrix != 0;
   const int ntiles = (n + TR - 1) / TR;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int r0 = t * TR;
     W a[RPT];
-    sell_rows<S, W, RPT>(meta, ci, av, nslices, r0, xval, a);
+    sell_rows<S, W, RPT>(meta, ci, av, nslices, r0, xval, a, ms);
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int row = r0 + threadIdx.x + k * NT;
