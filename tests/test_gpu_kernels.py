@@ -25,10 +25,22 @@ def _irregular(n=3000, seed=9):
     return gen.Problem("irregular", n, rp.astype(np.int32), cols, vals)
 
 
+def _wide(n=40000, seed=10):
+    """Five random columns per row anywhere in [0, n) plus the diagonal: |column - row| reaches
+    past 32767, so the plan keeps 32-bit column entries in its SELL copy."""
+    g = np.random.default_rng(seed)
+    cols = np.sort(np.concatenate([g.integers(0, n, (n, 5)), np.arange(n)[:, None]], axis=1), axis=1)
+    vals = g.standard_normal((n, 6))
+    vals[cols == np.arange(n)[:, None]] = 8.0
+    rp = np.arange(0, 6 * n + 1, 6, dtype=np.int32)
+    return gen.Problem("wide", n, rp, cols.ravel().astype(np.int32), vals.ravel())
+
+
 PROBLEMS = {
     "2d": lambda: gen.conv_diff_2d(71, 25.0, (0.6, 0.8)),
     "3d": lambda: gen.conv_diff_3d(17, 10.0, (1.0, -2.0, 0.5)),
     "irregular": _irregular,
+    "wide": _wide,
 }
 
 

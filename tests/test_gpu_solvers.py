@@ -370,3 +370,26 @@ def test_profile_cycle_times_every_kernel_of_one_cycle(g, torch, graph):
         ms2 = plan.profile_cycle(bt, x0, graph=graph)
         assert int((ms2[:-1, 0] >= 0).sum()) == k
         plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_ir_with_long_range_columns(g, torch, prec):
+    """A matrix whose columns lie up to n - 1 away from the diagonal (the plan's SELL copy
+    keeps 32-bit column entries; stencil matrices get 16-bit offsets): GMRES-IR solves it to
+    1e-10 and agrees with the oracle's FP64 GMRES."""
+    n = 40000
+    r = np.random.default_rng(10)
+    cols = np.sort(np.concatenate([r.integers(0, n, (n, 5)), np.arange(n)[:, None]], axis=1), axis=1)
+    vals = r.standard_normal((n, 6))
+    vals[cols == np.arange(n)[:, None]] = 8.0
+    p = gen.Problem("wide", n, np.arange(0, 6 * n + 1, 6, dtype=np.int32),
+                    cols.ravel().astype(np.int32), vals.ravel())
+    assert np.abs(cols - np.arange(n)[:, None]).max() > 32767
+    b = np.ones(n)
+    A = g.DeviceCSR.from_problem(p)
+    bt, xt = _dev(torch, b, np.zeros(n))
+    res = g.gmres_ir_solve(A, bt, xt, restart_m=30, rtol=1e-10, inner_prec=prec)
+    assert res.status == g.OK and res.relres <= 1e-10
+    xo, _ = oracle.gmres(p, b, m=30, rtol=1e-12)
+    x = xt.cpu().numpy()
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-8
