@@ -116,3 +116,29 @@ def test_fp64_gmres_with_fp32_polynomial(g, torch):
     r64 = g.gmres_solve(A, bt, xt.zero_(), restart_m=30, rtol=1e-10, poly_degree=10, seed=7,
                         max_iters=20000)
     assert abs(r.iters - r64.iters) <= 30
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_polynomial_path_with_a_matrix_larger_than_l2(g, torch, prec):
+    """On a 1500^2 anisotropic problem the inner copy of A (90 MB in FP32) and the
+    polynomial's vectors exceed three quarters of the L2, so the plan streams the matrix
+    through the polynomial's SpMVs evict-first: the apply still matches the emulated oracle
+    (FP32) and GMRES-IR with the degree-10 polynomial reaches 1e-10 by the oracle's explicit
+    residual."""
+    p, b = gen.config_aniso_2d(side=1500)
+    A = g.DeviceCSR.from_problem(p)
+    plan = g.Plan(A, "ir", restart_m=50, inner_prec=prec, poly_degree=10, seed=7, max_iters=20000)
+    if prec == "fp32":
+        pm = oracle.Precision("fp32", "fp32", p.n)
+        a32 = pm.matrix_values(p.vals)
+        op = lambda v: pm.rw(oracle.spmv(p, v, a32))
+        v = oracle.splitmix64_uniform(3, p.n)
+        z = plan.poly_apply(torch.tensor(v, device="cuda")).double().cpu().numpy()
+        zo = oracle.poly_apply(op, plan.roots(), pm.rw(v), pm.rw)
+        assert np.linalg.norm(z - zo) <= 1e-5 * np.linalg.norm(zo)
+    bt, xt = _dev(torch, b, np.zeros(p.n))
+    res = plan.solve(bt, xt)
+    assert res.status == g.OK
+    x = xt.cpu().numpy()
+    assert np.linalg.norm(b - oracle.spmv(p, x)) / np.linalg.norm(b) <= 1.0001e-10
+    plan.close()
