@@ -285,6 +285,14 @@ int gmres_plan_profile_cycle(gmres_plan plan, const double* b, const double* x0,
  * graph per call (not for use inside a solve loop); synchronises the stream. */
 int gmres_plan_profile_cycle_graph(gmres_plan plan, const double* b, const double* x0,
                                    double* ms_out, void* stream);
+/* The cycle of gmres_plan_profile_cycle_graph captured with event-record nodes only
+ * before its first kernel and after its last, so that no event node sits between two
+ * kernels: ms_out (HOST, 2 doubles) = {milliseconds of the whole cycle, Arnoldi steps
+ * it took}.  With the per-kernel times of gmres_plan_profile_cycle_graph this gives each
+ * kernel's share of a cycle that runs as in a solve.  Same inputs, state reset and
+ * synchronisation as gmres_plan_profile_cycle_graph. */
+int gmres_plan_time_cycle_graph(gmres_plan plan, const double* b, const double* x0,
+                                double* ms_out, void* stream);
 
 /* Plan geometry: info_out (HOST, 8 int64) = n, nnz, leading dimension ld,
  * m, storage precision, grid of the SpMV kernel, grid of the CGS kernels,

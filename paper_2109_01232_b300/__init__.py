@@ -102,6 +102,7 @@ _SIGNATURES = {
     "gmres_splitmix64_fill": (ctypes.c_int, [_P, _I64, _U64, _P]),
     "gmres_plan_profile_cycle": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gmres_plan_profile_cycle_graph": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gmres_plan_time_cycle_graph": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gmres_plan_info": (ctypes.c_int, [_P, _P]),
     "gmres_plan_poly_apply": (ctypes.c_int, [_P, _P, _P, _P]),
     "gmres_plan_poly_roots": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
@@ -401,6 +402,14 @@ class Plan:
         fn = lib().gmres_plan_profile_cycle_graph if graph else lib().gmres_plan_profile_cycle
         _check(fn(self.handle, _ptr(b), _ptr(x0), out.ctypes.data, _stream(stream)), "profile_cycle")
         return out.reshape(m + 1, 3)
+
+    def time_cycle(self, b, x0, stream=None) -> tuple:
+        """(ms, steps) of one cycle run as a captured graph with events only at its two ends
+        (no event node between kernels)."""
+        out = np.zeros(2, dtype=np.float64)
+        _check(lib().gmres_plan_time_cycle_graph(self.handle, _ptr(b), _ptr(x0), out.ctypes.data,
+                                                 _stream(stream)), "time_cycle")
+        return float(out[0]), int(out[1])
 
     def close(self):
         if self.handle:

@@ -151,7 +151,7 @@ __device__ __forceinline__ void sell_products(const int (&ci)[EB][R], const AT (
   for (int eb = 0; eb < EB; ++eb) {
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (ci[eb][k] >= 0) acc[k] += to_w(va[eb][k]) * xv[eb][k];
+      if (ci[eb][k] >= 0) acc[k] += (W)to_w(va[eb][k]) * xv[eb][k];
   }
 }
 
@@ -1079,7 +1079,7 @@ __global__ void __launch_bounds__(NT) k_finalize(StepParts<typename Tr<P>::W> pa
 __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* Rs = reinterpret_cast<double*>(smem_raw);
-  __shared__ double gw[LSQ_MAX + 1];
+  __shared__ double gw[LSQ_MAX + 1], cs_s[LSQ_MAX], sn_s[LSQ_MAX], rinv[LSQ_MAX];
   __shared__ double red[NWARP];
   __shared__ int s_kk, s_skip;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1088,6 +1088,16 @@ __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) 
   if (s_skip) return;
   const int k = st->k, ldh = st->m + 1;
   auto rix = [](int i, int c) { return c * (c + 1) / 2 + i; };
+  // All loads of R and of the rotations are issued by the whole block at once; the serial
+  // parts below read shared memory only.
+  // The divisions by the diagonal are done here, all at once: the substitution below
+  // multiplies by these reciprocals, so its serial chain holds no FP64 division (slow to
+  // issue on this part); y_i = g_i (1 / r_ii) carries one rounding more than g_i / r_ii.
+  for (int i = tid; i < k; i += NT) {
+    cs_s[i] = a.cs[i];
+    sn_s[i] = a.sn[i];
+    rinv[i] = 1.0 / a.R[i + (long long)i * ldh];
+  }
   double rmax = 0.0;
   for (int c = warp; c < k; c += NWARP)
     for (int i = lane; i <= c; i += 32) {
@@ -1101,8 +1111,8 @@ __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) 
   if (tid == 0) {
     double g = 1.0;  // g_0 = 1 (unit least-squares right-hand side)
     for (int i = 0; i < k; ++i) {
-      gw[i] = a.cs[i] * g;
-      g = -a.sn[i] * g;
+      gw[i] = cs_s[i] * g;
+      g = -sn_s[i] * g;
     }
     double mx = 0.0;
     for (int w = 0; w < NWARP; ++w) mx = fmax(mx, red[w]);
@@ -1117,8 +1127,7 @@ __global__ void __launch_bounds__(NT) k_lsq(DevState* st, Arrays a, int packed) 
   if (warp != 0) return;
   const int kk = s_kk;
   for (int i = kk - 1; i >= 0; --i) {
-    const double rii = packed ? Rs[rix(i, i)] : a.R[i + (long long)i * ldh];
-    const double yi = gw[i] / rii;
+    const double yi = gw[i] * rinv[i];
     __syncwarp();
     for (int l = lane; l < i; l += 32)
       gw[l] -= (packed ? Rs[rix(l, i)] : a.R[l + (long long)i * ldh]) * yi;
@@ -1187,23 +1196,24 @@ __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict
 // "r_{i+1} = b - A x_{i+1} [double]").
 // ---------------------------------------------------------------------------
 constexpr int RES_TR = NT * 2;
-constexpr int RES_CAP = 4096;  // nonzeros staged per chunk (32 KB)
-inline size_t residual_smem() { return sizeof(double) * RES_CAP + sizeof(int) * (RES_TR + 1) + 16; }
 
+// The matrix is the SELL-32 layout of the inner copy (same slices and columns) with FP64
+// values: sv = A's values unscaled, in CSR order within each row, so every row's sum takes
+// its entries in the order of the CSR input.  The SELL form keeps every load of the matrix
+// coalesced and needs no shared-memory staging or barrier per tile.  The matrix is read once
+// per call and is streamed evict-first.
 // F32: the residual of GMRES run entirely in single precision (GMRES-FD's first stage,
 // Section 3.3): b, A and x rounded to FP32 and the products and sums in FP32; the result
 // is stored in the FP64 vector r and its norms accumulated in FP64.
 template <bool F32>
-__global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, const int* __restrict__ ci,
-                                                 const double* __restrict__ av, int n,
-                                                 const double* __restrict__ x,
-                                                 const double* __restrict__ b, double* __restrict__ r,
-                                                 double* __restrict__ part, DevState* st, Arrays arr,
-                                                 int first) {
+__global__ void __launch_bounds__(NT, 2) k_residual(const int2* __restrict__ meta, const int* __restrict__ sc,
+                                                    const double* __restrict__ sv, int nslices, int n,
+                                                    const double* __restrict__ x,
+                                                    const double* __restrict__ b, double* __restrict__ r,
+                                                    double* __restrict__ part, DevState* st, Arrays arr,
+                                                    int first) {
   using RW = typename std::conditional<F32, float, double>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  RW* prod_s = reinterpret_cast<RW*>(smem_raw);
-  int* rp_s = reinterpret_cast<int*>(smem_raw + sizeof(double) * RES_CAP);
+  constexpr int RPT = RES_TR / NT;
   __shared__ double red_r[NWARP], red_b[NWARP];
   __shared__ int s_skip, s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1215,10 +1225,10 @@ __global__ void __launch_bounds__(NT) k_residual(const int* __restrict__ rp, con
   const int ntiles = (n + RES_TR - 1) / RES_TR;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int r0 = t * RES_TR;
-    RW a[RES_TR / NT];
-    tile_spmv<double, RW, RES_TR, RES_CAP>(rp, ci, av, n, r0, rp_s, prod_s, xval, a);
+    RW a[RPT];
+    sell_rows<double, RW, RPT>(meta, sc, sv, nslices, r0, xval, a, true);
 #pragma unroll
-    for (int k = 0; k < RES_TR / NT; ++k) {
+    for (int k = 0; k < RPT; ++k) {
       const int row = r0 + tid + k * NT;
       if (row < n) {
         const RW bv = (RW)b[row];
@@ -1314,7 +1324,8 @@ __global__ void k_cast_vals(const double* __restrict__ v, S* __restrict__ out, l
 
 // Fill the SELL-32 copy from CSR: one thread per (padded) row.  Values are divided by
 // `scale` and rounded to the storage type; padding entries get value 0 and an in-range
-// column (the row itself, or 0 past the last row).
+// column (the row itself, or 0 past the last row).  sc == nullptr: values only (a second
+// value array over columns already written).
 template <class S>
 __global__ void k_build_sell(const int* __restrict__ rp, const int* __restrict__ ci,
                              const double* __restrict__ v, int n, const int2* __restrict__ meta,
@@ -1330,10 +1341,10 @@ __global__ void k_build_sell(const int* __restrict__ rp, const int* __restrict__
     for (int e = 0; e < mt.y; ++e) {
       const long long idx = (long long)mt.x + (long long)e * 32 + l;
       if (e < len) {
-        sc[idx] = ci[base + e];
+        if (sc) sc[idx] = ci[base + e];
         sv[idx] = to_s<S>(v[base + e] / scale);
       } else {
-        sc[idx] = pad_col;
+        if (sc) sc[idx] = pad_col;
         sv[idx] = to_s<S>(0.0);
       }
     }

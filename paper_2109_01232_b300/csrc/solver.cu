@@ -91,6 +91,7 @@ struct Plan {
   void *pa = nullptr, *pb = nullptr, *pt = nullptr, *py = nullptr;  // working-type vectors
   bool poly32 = false;           // FP64 cycle, polynomial applied in FP32
   void* sell_vals32 = nullptr;   // FP32 values of the SELL copy (poly32)
+  void* sell_vals64 = nullptr;   // FP64 values of the SELL copy (residual of non-FP64 plans)
   // block-Jacobi preconditioner (right) and the reverse Cuthill-McKee reordering
   int bj = 0;                    // block size k; 0 = none
   void* bj_lu = nullptr;         // factors of the diagonal blocks (working type, k*k per block)
@@ -289,14 +290,15 @@ static void launch_step(Plan& pl, int j, cudaStream_t s) {
 }
 
 static void launch_residual(Plan& pl, int first, cudaStream_t s) {
+  const double* av = (const double*)(pl.prec == GMRES_FP64 ? pl.sell_vals : pl.sell_vals64);
   if (pl.kind == 2)  // single-precision GMRES: FP32 residual
-    k_residual<true><<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals,
-                                                             pl.n, pl.xb, pl.bb, pl.r, (double*)pl.part,
-                                                             pl.st, pl.arr, first);
+    k_residual<true><<<pl.grid_res, NT, 0, s>>>(pl.sell_meta, pl.sell_cols, av, pl.nslices, pl.n,
+                                                pl.xb, pl.bb, pl.r, (double*)pl.part, pl.st, pl.arr,
+                                                first);
   else
-    k_residual<false><<<pl.grid_res, NT, residual_smem(), s>>>(pl.A.row_ptr, pl.A.col_idx, pl.A.vals,
-                                                              pl.n, pl.xb, pl.bb, pl.r, (double*)pl.part,
-                                                              pl.st, pl.arr, first);
+    k_residual<false><<<pl.grid_res, NT, 0, s>>>(pl.sell_meta, pl.sell_cols, av, pl.nslices, pl.n,
+                                                 pl.xb, pl.bb, pl.r, (double*)pl.part, pl.st, pl.arr,
+                                                 first);
 }
 
 // Kernel `which` of the cycle's end (0: least squares, 1: x update -- x += gamma p(A) V y
@@ -409,7 +411,7 @@ static int configure(Plan& pl) {
 
 static int configure_residual(Plan& pl) {
   int occ = 1;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<false>, NT, residual_smem()));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_residual<false>, NT, 0));
   const long long ntiles = (pl.n + RES_TR - 1) / RES_TR;
   pl.grid_res = (int)std::max(1LL, std::min(ntiles, (long long)std::min(std::max(occ, 1), 2) * pl.sms));
   return GMRES_OK;
@@ -449,6 +451,7 @@ static void plan_free(Plan* pl) {
   cudaFree(pl->part);
   cudaFree(pl->pa);
   cudaFree(pl->sell_vals32);
+  cudaFree(pl->sell_vals64);
   cudaFree(pl->pb);
   cudaFree(pl->pt);
   cudaFree(pl->py);
@@ -674,6 +677,13 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
                                              pl->a_scale, pl->sell_cols, (S*)pl->sell_vals);
       return 0;
     });
+    // The FP64 residual reads A in the same SELL layout with its FP64 values (an FP64
+    // plan's copy already is that).
+    if (pl->prec != GMRES_FP64) {
+      if ((e = alloc(&pl->sell_vals64, 8 * (size_t)std::max(off, 1LL)))) return fail(e);
+      k_build_sell<double><<<blocks, 256, 0, s>>>(rp, ci, va, pl->n, pl->sell_meta, pl->nslices, 1.0,
+                                                  nullptr, (double*)pl->sell_vals64);
+    }
     // the meta upload reads `meta` asynchronously: finish before it goes out of scope
     if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   }
@@ -705,7 +715,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     if (pl->poly32) {  // FP32 copy of the SELL values for the polynomial
       if ((e = alloc(&pl->sell_vals32, 4 * (size_t)std::max(pl->sell_nnz, 1LL)))) return fail(e);
       k_build_sell<float><<<pl->sms * 8, 256, 0, s>>>(A->row_ptr, A->col_idx, A->vals, pl->n,
-                                                     pl->sell_meta, pl->nslices, 1.0, pl->sell_cols,
+                                                     pl->sell_meta, pl->nslices, 1.0, nullptr,
                                                      (float*)pl->sell_vals32);
       if (int e_ = CUDA_STATUS(cudaGetLastError())) return fail(e_);
     }
@@ -1018,8 +1028,11 @@ int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_o
 // time between the events around kernel i as it runs inside a graph, the way a solve runs
 // it (layout as plan_profile_cycle; -1 for the steps the cycle did not reach, whose kernels
 // returned at once).  Costs one graph instantiation per call.
+// per_kernel == false: the same graph with only the first and the last event node, so no
+// event sits between two kernels; ms_out[0] = the whole cycle (residual of the next cycle
+// included), ms_out[1] = the Arnoldi steps it took.
 int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double* ms_out,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool per_kernel = true) {
   const int m = pl.m, nslots = 3 * m + 3;
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
@@ -1048,11 +1061,11 @@ int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double
     constexpr int P = decltype(PP)::value;
     for (int j = 0; j < m; ++j)
       for (int w = 0; w < 3; ++w) {
-        cudaEventRecordWithFlags(ev[3 * j + w], cs, cudaEventRecordExternal);
+        if (per_kernel || j + w == 0) cudaEventRecordWithFlags(ev[3 * j + w], cs, cudaEventRecordExternal);
         launch_step_kernel<P>(pl, j, w, cs);
       }
     for (int w = 0; w < 3; ++w) {
-      cudaEventRecordWithFlags(ev[3 * m + w], cs, cudaEventRecordExternal);
+      if (per_kernel) cudaEventRecordWithFlags(ev[3 * m + w], cs, cudaEventRecordExternal);
       launch_tail_kernel<P>(pl, w, cs);
     }
     cudaEventRecordWithFlags(ev[nslots], cs, cudaEventRecordExternal);
@@ -1060,6 +1073,9 @@ int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double
   });
   if ((err = CUDA_STATUS(cudaStreamEndCapture(cs, &graph)))) return done(err);
   if ((err = CUDA_STATUS(cudaGraphInstantiate(&exec, graph, 0)))) return done(err);
+  // upload the graph before the timed launch, so that its first launch does not include it
+  if ((err = CUDA_STATUS(cudaGraphUpload(exec, s)))) return done(err);
+  if ((err = CUDA_STATUS(cudaStreamSynchronize(s)))) return done(err);
   if ((err = CUDA_STATUS(cudaGraphLaunch(exec, s)))) return done(err);
   if ((err = CUDA_STATUS(cudaMemcpyAsync(pl.h_st, pl.st, sizeof(DevState), cudaMemcpyDeviceToHost, s))))
     return done(err);
@@ -1067,6 +1083,13 @@ int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double
   // Arnoldi steps the cycle took (the solve's step count starts at zero in init_state;
   // st->k is already reset for the next cycle by the residual kernel)
   const long long steps = pl.h_st->iters;
+  if (!per_kernel) {
+    float ms = -1.f;
+    if ((err = CUDA_STATUS(cudaEventElapsedTime(&ms, ev[0], ev[nslots])))) return done(err);
+    ms_out[0] = ms;
+    ms_out[1] = (double)steps;
+    return done(GMRES_OK);
+  }
   for (int i = 0; i < nslots; ++i) {
     const bool ran = i >= 3 * m || i / 3 < steps;
     float ms = -1.f;
@@ -1205,6 +1228,12 @@ int gmres_plan_profile_cycle_graph(gmres_plan plan, const double* b, const doubl
                                    double* ms_out, void* stream) {
   if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
   return gm::plan_profile_cycle_graph(*plan->pl, b, x0, ms_out, (cudaStream_t)stream);
+}
+
+int gmres_plan_time_cycle_graph(gmres_plan plan, const double* b, const double* x0,
+                                double* ms_out, void* stream) {
+  if (!plan || !b || !x0 || !ms_out) return GMRES_ERR_INVALID;
+  return gm::plan_profile_cycle_graph(*plan->pl, b, x0, ms_out, (cudaStream_t)stream, false);
 }
 
 int gmres_plan_poly_apply(gmres_plan plan, const double* v, void* y, void* stream) {

@@ -372,11 +372,33 @@ def test_profile_cycle_times_every_kernel_of_one_cycle(g, torch, graph):
         plan.close()
 
 
+def test_time_cycle_matches_the_profiled_cycle(g, torch):
+    """The uninstrumented cycle timer runs the same cycle as the per-kernel profile (same
+    step count, the full m here and fewer with an inner tolerance) and, for a full cycle,
+    takes less time than the sum of the per-kernel event intervals, whose event nodes sit
+    between the kernels.  (A cycle that ends early still launches the remaining steps'
+    kernels, which return at once: the uninstrumented time includes them, the profile
+    reports -1 for them.)"""
+    p, b, _ = gen.config_small_2d(48)
+    A = g.DeviceCSR.from_problem(p)
+    bt, x0 = _dev(torch, b, np.zeros(p.n))
+    for m, inner_rtol in ((20, 0.0), (40, 1e-2)):
+        plan = g.Plan(A, "ir", restart_m=m, inner_rtol=inner_rtol)
+        ms = plan.profile_cycle(bt, x0, graph=True)
+        k = int((ms[:-1, 0] >= 0).sum())
+        t, steps = plan.time_cycle(bt, x0)
+        assert steps == k and (k == m) == (inner_rtol == 0.0)
+        assert t > 0.0
+        if k == m:
+            assert t < ms.sum()
+        plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_ir_with_long_range_columns(g, torch, prec):
-    """A matrix whose columns lie up to n - 1 away from the diagonal (the plan's SELL copy
-    keeps 32-bit column entries; stencil matrices get 16-bit offsets): GMRES-IR solves it to
-    1e-10 and agrees with the oracle's FP64 GMRES."""
+    """A matrix whose columns lie up to n - 1 away from the diagonal (the SELL copy's column
+    entries span the whole index range): GMRES-IR solves it to 1e-10 and agrees with the
+    oracle's FP64 GMRES."""
     n = 40000
     r = np.random.default_rng(10)
     cols = np.sort(np.concatenate([r.integers(0, n, (n, 5)), np.arange(n)[:, None]], axis=1), axis=1)
