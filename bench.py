@@ -388,7 +388,10 @@ def run_ours(args, rank, world, local_rank):
                 raise SystemExit(f"solve failed: {r}")
     ir_iters = {f"pe{it['pe']:g}": r.iters for it, r in zip(insts, results[-1])}
     ir_relres = {f"pe{it['pe']:g}": r.relres for it, r in zip(insts, results[-1])}
-    launches_per_step = sum(1 + r.outer * (3 * M + 3) for r in results[-1])
+    # per solve: the first residual, then per refinement step one cycle graph of 3 kernels per
+    # Arnoldi step, the store of v_0 (low-precision cycles), the last Givens update, least
+    # squares, x update and residual
+    launches_per_step = sum(1 + r.outer * (3 * M + 5) for r in results[-1])
 
     # FP64 GMRES(50) on the same GPU (the comparison named by the metric).
     for it in insts:

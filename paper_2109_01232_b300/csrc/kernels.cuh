@@ -926,8 +926,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
 // an Arnoldi run that is not followed by another SpMV).
 template <int P, class SrcT>
 __global__ void k_store_basis(const SrcT* __restrict__ src, double v_scale, int n,
-                              typename Tr<P>::S* V, long long ld, int j, const DevState* st) {
+                              typename Tr<P>::S* V, long long ld, int j, const DevState* st,
+                              int in_cycle = 0) {
   using S = typename Tr<P>::S;
+  if (in_cycle && read_flag(&st->stop)) return;  // (the start of a cycle that is not run)
   const SrcT f = (SrcT)(v_scale * st->sigma);
   S* Vj = V + (long long)j * ld;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;

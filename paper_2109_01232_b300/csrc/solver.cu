@@ -251,7 +251,16 @@ static void launch_step_kernel(Plan& pl, int j, int which, cudaStream_t s) {
       return;
     }
     const double rs = pl.a_scale / pl.v_scale;
-    if (j == 0)
+    if (j == 0 && P != GMRES_FP64) {
+      // v_0 = store(v_scale sigma r) from the FP64 residual: formed once per row here (FP64
+      // products issue slowly on this part), then the SpMV gathers the stored v_0 as a
+      // preconditioned SpMV gathers its input (the same values as forming them per gather)
+      k_store_basis<P, double><<<pl.grid_elem, NT, 0, s>>>(pl.r, pl.v_scale, pl.n, V, pl.ld, 0,
+                                                          pl.st, 1);
+      k_spmv_sell<P, S, true><<<pl.grid_spmv, NT, sm1, s>>>(
+          pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs,
+          (const S*)V, pl.v_scale, V, 0, w1, sp, pl.st, pl.arr);
+    } else if (j == 0)
       k_spmv_sell<P, double, false><<<pl.grid_spmv, NT, sm1, s>>>(
           pl.sell_meta, pl.sell_cols, (const S*)pl.sell_vals, pl.nslices, pl.n, pl.ld, rs, pl.r,
           pl.v_scale, V, 0, w1, sp, pl.st, pl.arr);
@@ -373,6 +382,7 @@ static int cluster_grid(K* kernel, size_t smem, long long want, int* grid) {
 
 template <int P>
 static int configure(Plan& pl) {
+  using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
   constexpr int VEC = Tr<P>::VEC;
   // The attributes are per kernel, shared by every plan: set them for the largest restart
@@ -386,6 +396,8 @@ static int configure(Plan& pl) {
   CK(cudaFuncSetAttribute(k_spmv_sell<P, W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_attr));
   CK(cudaFuncSetAttribute(k_spmv_sell<P, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)sm_attr));
+  CK(cudaFuncSetAttribute(k_spmv_sell<P, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)sm_attr));
   const size_t sm_u1 = sizeof(W) * (size_t)(pl.m + 1) * (1 + NWARP);
   CK(cudaFuncSetAttribute(k_cgs_u1<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -767,8 +779,9 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     pl->t_setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb0).count();
   }
 
-  // L2 policy of the SpMVs that follow a preconditioner: block Jacobi reads the matrix once
-  // per step, so it is streamed evict-first like the plain cycle's; the polynomial re-reads
+  // L2 policy of the SpMVs that gather a stored input (after a preconditioner, and the first
+  // step of a plain low-precision cycle): block Jacobi and the plain cycle read the matrix once
+  // per step, so it is streamed evict-first like the other steps'; the polynomial re-reads
   // it d times per step, which pays while the copy of A and the polynomial's vectors stay in
   // L2 (measured: 100^3, 56 MB FP32 copy, degree 10/25, streaming 17-28% slower; 2000^2,
   // 160 MB FP32 / 120 MB FP16 copy, degree 40, streaming 24% faster).
@@ -779,7 +792,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     const double vals = pl->poly32 ? 4.0 : (double)storage_bytes(pl->prec);
     const double work = pl->poly32 ? 4.0 : (double)work_bytes(pl->prec);
     const double bytes = (double)pl->sell_nnz * (4.0 + vals) + 4.0 * work * (double)pl->n;
-    pl->stream_matrix = pl->bj ? 1 : (!pl->poly.empty() && bytes > 0.75 * (double)l2 ? 1 : 0);
+    pl->stream_matrix = pl->poly.empty() ? 1 : (bytes > 0.75 * (double)l2 ? 1 : 0);
   }
 
   // Capture one restart cycle as a CUDA graph.
