@@ -230,11 +230,38 @@ __device__ __forceinline__ void sell_rows(const int2* __restrict__ meta, const i
 }
 
 // Sum of the G per-CTA partials p[0..G) by one warp, four independent load streams per
-// lane (fixed order, so the result is reproducible).
+// lane (fixed order, so the result is reproducible).  Up to 320 partials (two CTAs per SM
+// on 148 SMs give at most 296) all of a lane's loads are issued at once, one L2 round trip,
+// and summed in the order of the general loop below (bitwise the same result).
 template <class W>
 __device__ __forceinline__ W warp_sum_partials(const W* __restrict__ p, int G) {
   const int lane = threadIdx.x & 31;
   W s0 = W(0), s1 = W(0), s2 = W(0), s3 = W(0);
+  if (G <= 320) {
+    W v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const int b = lane + 32 * k;
+      v[k] = k < 10 && b < G ? __ldcg(&p[b]) : W(0);
+    }
+    bool wide = true;  // still in the four-stream loop
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int b = lane + 128 * i;
+      if (wide && b + 96 < G) {
+        s0 += v[4 * i];
+        s1 += v[4 * i + 1];
+        s2 += v[4 * i + 2];
+        s3 += v[4 * i + 3];
+      } else {
+        wide = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (b + 32 * q < G) s0 += v[4 * i + q];
+      }
+    }
+    return warp_sum((s0 + s1) + (s2 + s3));
+  }
   int b = lane;
   for (; b + 96 < G; b += 128) {
     s0 += __ldcg(&p[b]);
