@@ -56,7 +56,8 @@ typedef enum {
 
 /* Storage precision of the inner solve: the Krylov basis V and the copy of A
  * used by the inner SpMV.  FP16/BF16 store 16-bit values and accumulate in
- * FP32; FP16 scales A by 1/max|a_ij| and each basis vector by sqrt(n). */
+ * FP32; FP16 scales A by 1/max|a_ij| and each basis vector by s_v, the largest
+ * power of two with s_v^2 <= 2n (about sqrt(n)). */
 typedef enum { GMRES_FP64 = 0, GMRES_FP32 = 1, GMRES_FP16 = 2, GMRES_BF16 = 3 } gmres_prec;
 
 /* CSR matrix, FP64 values (the master copy used by every FP64 residual).
@@ -217,7 +218,7 @@ int gmres_plan_spmv(gmres_plan plan, const double* v, void* y, void* stream);
 /* Arnoldi with CGS2 from v0 (DEVICE, n doubles) for `steps` steps (<= m),
  * the cycle kernels of the solver without the stopping test.  V_out: DEVICE,
  * (steps+1) columns of n values in the storage type (double, float, half or
- * bfloat16; FP16 values are scaled by sqrt(n)).  H_out: HOST, (steps+1) x
+ * bfloat16; FP16 values are scaled by s_v, see gmres_prec).  H_out: HOST, (steps+1) x
  * steps FP64, column-major.  *k_out = steps taken (fewer after a breakdown). */
 int gmres_plan_arnoldi(gmres_plan plan, const double* v0, int32_t steps, void* V_out,
                        double* H_out, int32_t* k_out, void* stream);

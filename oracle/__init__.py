@@ -13,7 +13,7 @@ sizes and iteration-count structure.
 """
 from .gmres import (  # noqa: F401
     OK, NOT_CONVERGED, BREAKDOWN, NONFINITE, INVALID,
-    Precision, Cycle, Info,
+    Precision, Cycle, Info, vector_scale,
     spmv, dense, cgs2, givens, back_substitute, gmres_cycle, arnoldi,
     gmres, gmres_ir, gmres_fd,
 )

@@ -40,8 +40,10 @@ Readings where the paper is silent:
   m steps (the paper's behaviour: IR iteration counts are multiples of m);
   inner_rtol > 0 ends the cycle when |g_{j+1}| <= inner_rtol.
 * Low-precision storage (IR): the copy of A is stored as round(A / s_A) and
-  basis vectors as round(s_v v) / s_v, with s_A = max|a_ij| and s_v = sqrt(n)
-  for FP16 (range) and s_A = s_v = 1 otherwise; products accumulate in FP32.
+  basis vectors as round(s_v v) / s_v, with s_A = max|a_ij| and s_v the largest
+  power of two with s_v^2 <= 2n (within a factor sqrt(2) of sqrt(n): the entries of
+  a unit vector, ~1/sqrt(n), are held near 1) for FP16 and s_A = s_v = 1 otherwise;
+  products accumulate in FP32.  Scaling by a power of two adds no rounding.
 """
 from __future__ import annotations
 
@@ -79,6 +81,13 @@ def dense(A) -> np.ndarray:
 # Precision model of the inner solver
 # --------------------------------------------------------------------------
 
+def vector_scale(n: int) -> float:
+    """FP16 basis scale: the largest power of two s with s^2 <= 2n (exact integers)."""
+    k = ((2 * max(int(n), 1)).bit_length() - 1) // 2
+    return float(2 ** k)
+
+
+
 @dataclass
 class Precision:
     """Storage format of the Krylov basis and of the low-precision copy of A, plus the
@@ -98,7 +107,7 @@ class Precision:
         s_A, s_v = 1.0, 1.0
         if storage == "fp16":
             s_A = float(np.max(np.abs(A.vals))) if A.vals.size else 1.0
-            s_v = float(np.sqrt(A.n))
+            s_v = vector_scale(A.n)
         return Precision(storage, work, A.n, s_A, s_v)
 
     def store_vector(self, v: np.ndarray) -> np.ndarray:

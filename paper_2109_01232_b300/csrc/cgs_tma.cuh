@@ -203,8 +203,8 @@ __device__ __forceinline__ bool tma_prologue(DevState* st, const typename Tr<P>:
   if (tid < TMA_RB) {
     const bool writer = blockIdx.x == 0;
     block_reduce_columns<TMA_CW>(part, nc, G, [&](int c, typename Tr<P>::W v) {
-      const double hc = (double)v / v_scale;
-      coef[c] = (typename Tr<P>::W)(hc / v_scale);
+      const double hc = (double)v * pow2_recip(v_scale);
+      coef[c] = (typename Tr<P>::W)(hc * pow2_recip(v_scale));
       if (writer) h[c] = hc;
     });
     consumers_sync();

@@ -32,6 +32,12 @@ template <> struct Tr<2> { using S = __half;        using W = float;  static con
 template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4; static constexpr bool V_EF = false; };
 
 // storage -> working type
+// 1 / v for v an exact power of two in the normal range (the basis scale v_scale): the
+// exponent is mirrored, so x * pow2_recip(v) == x / v exactly, without an FP64 division
+// (slow to issue on this part).
+__device__ __forceinline__ double pow2_recip(double v) {
+  return __longlong_as_double(0x7FE0000000000000LL - __double_as_longlong(v));
+}
 __device__ __forceinline__ double to_w(double v) { return v; }
 __device__ __forceinline__ float to_w(float v) { return v; }
 __device__ __forceinline__ float to_w(__half v) { return __half2float(v); }

@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
   }
   if (!arrive_last(&st->ticket[0], &s_last)) return;
   block_reduce_columns(part, ncol, G, [&](int c, W s) {
-    if (c <= j) h1[c] = (double)s / v_scale;
+    if (c <= j) h1[c] = (double)s * pow2_recip(v_scale);
     else st->wnorm = sqrt((double)s);
   });
   if (tid == 0) st->ticket[0] = 0;
@@ -972,9 +972,10 @@ template <class W>
 __device__ __forceinline__ void coefs_from_sums(W* coef, int nc, double v_scale,
                                                 double* __restrict__ h) {
   const bool writer = blockIdx.x == 0;
+  const double r = pow2_recip(v_scale);
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    const double hc = (double)coef[c] / v_scale;
-    coef[c] = (W)(hc / v_scale);
+    const double hc = (double)coef[c] * r;
+    coef[c] = (W)(hc * r);
     if (writer) h[c] = hc;
   }
   __syncthreads();
@@ -1186,7 +1187,7 @@ __global__ void __launch_bounds__(NT) k_xupd(const typename Tr<P>::S* __restrict
   if (tid == 0) {
     s_skip = read_flag(&st->stop);
     s_kk = st->k_used;
-    s_fac = st->gamma / v_scale;
+    s_fac = st->gamma * pow2_recip(v_scale);
   }
   __syncthreads();
   if (s_skip) return;

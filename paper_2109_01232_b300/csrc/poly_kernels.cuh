@@ -59,7 +59,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) k_poly_start(co
     sigma = st->sigma;
   }
   const SrcT f = (SrcT)(v_scale * sigma);
-  const W inv = (W)(1.0 / v_scale);
+  const W inv = (W)pow2_recip(v_scale);
   S* Vj = V + (long long)j * ld;
   for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
     const S v = to_s<S>(f * src[i]);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NT) k_vy(const typename Tr<P>::S* __restrict__
   const int kk = s_kk;
   for (int c = threadIdx.x; c < kk; c += NT) coef[c] = (W)y[c];
   __syncthreads();
-  const W inv = (W)(1.0 / v_scale);
+  const W inv = (W)pow2_recip(v_scale);
   const long long ngroups = ld / VEC;
   const long long g0 = cta_begin(ngroups, 32), g1 = cta_begin(ngroups, 32, 1);
   for (long long g = g0 + threadIdx.x; g < g1; g += NT) {

@@ -654,7 +654,10 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     memcpy(&mx, &bits, 8);
     if (!std::isfinite(mx)) return fail(GMRES_NONFINITE);
     pl->a_scale = mx > 0.0 ? mx : 1.0;
-    pl->v_scale = std::sqrt((double)pl->n);
+    // basis scale: the largest power of two s with s^2 <= 2n, within a factor sqrt(2) of
+    // sqrt(n) (unit vectors' entries held near 1); a power of two, so scaling adds no
+    // rounding and the kernels divide by it exactly with a multiplication
+    pl->v_scale = std::ldexp(1.0, (63 - __builtin_clzll(2ULL * (unsigned long long)std::max(pl->n, 1))) / 2);
   }
   {
     std::vector<int> hrp((size_t)pl->n + 1);

@@ -281,7 +281,11 @@ def test_ir_half_storage_converges(inner):
 def test_ir_fp16_scaling_keeps_stored_basis_in_range():
     p, b, _ = gen.config_small_2d(24)
     prec = oracle.Precision.for_inner("fp16", p)
-    assert prec.s_v == pytest.approx(np.sqrt(p.n))
+    # a power of two within a factor sqrt(2) of sqrt(n), so scaling adds no rounding
+    k = int(np.log2(prec.s_v))
+    assert prec.s_v == 2.0 ** k and np.sqrt(p.n / 2) < prec.s_v <= np.sqrt(2 * p.n)
+    assert [oracle.vector_scale(n) for n in (1, 2, 7, 8, 1000, 2048, 8192, 10**6)] == \
+        [1.0, 2.0, 2.0, 4.0, 32.0, 64.0, 128.0, 1024.0]
     assert prec.s_A == pytest.approx(np.abs(p.vals).max())
     v = np.ones(p.n) / np.sqrt(p.n)
     np.testing.assert_allclose(prec.store_vector(v), v, rtol=1e-3)
