@@ -200,6 +200,26 @@ def split(n: int, held_out: int, seed: int = 4999):
     return np.sort(perm[held_out:]), np.sort(perm[:held_out])
 
 
+CORPUS_N_HI, CORPUS_COUNT, CORPUS_HELD_OUT = 4e6, 400, 80
+
+
+def corpus_split(data: dict, held_out: int = CORPUS_HELD_OUT, seed: int = 4999):
+    """Train / held-out positions of a sweep that holds the whole configured corpus
+    (gen.selector_matrices(400, n_hi=4e6)): the held-out matrices are the corpus indices
+    permutation(400)[:80] of PCG64(seed); every other swept matrix trains, except a matrix of
+    another corpus drawn from the same seed as a held-out one (same dimension, Peclet
+    number, anisotropy and wind at another size), which is left out of both."""
+    nh, di, ds = data["desc_n_hi"], data["desc_index"], data["desc_seed"]
+    conf = nh == CORPUS_N_HI
+    if sorted(di[conf].tolist()) != list(range(CORPUS_COUNT)):
+        raise ValueError("the sweep does not hold every matrix of the configured corpus")
+    held_idx = np.random.Generator(np.random.PCG64(seed)).permutation(CORPUS_COUNT)[:held_out]
+    te = np.flatnonzero(conf & np.isin(di, held_idx))
+    held_seeds = ds[te]
+    tr = np.flatnonzero(~np.isin(np.arange(len(nh)), te) & ~(~conf & np.isin(ds, held_seeds)))
+    return tr, te
+
+
 def _ratio(times, t0):
     """Time relative to the default; failures count as the timeout factor."""
     r = times / t0
@@ -303,7 +323,8 @@ def main(argv=None):
     s4.add_argument("--n-max", type=float, default=2e6)
     s2 = sub.add_parser("fit")
     s2.add_argument("--sweep", default=SWEEP_PATH)
-    s2.add_argument("--held-out", type=float, default=0.2)
+    s2.add_argument("--held-out", type=float, default=0.2,
+                    help="share held out when the sweep lacks part of the configured corpus")
     s2.add_argument("--out", default=MODEL_PATH)
     a = ap.parse_args(argv)
     if a.cmd == "sweep":
@@ -336,7 +357,10 @@ def main(argv=None):
     else:
         data = load(a.sweep)
         n = len(data["default_ms"])
-        tr, te = split(n, int(round(a.held_out * n)))
+        try:
+            tr, te = corpus_split(data)
+        except ValueError:
+            tr, te = split(n, int(round(a.held_out * n)))
         model = fit(data, tr)
         model["held_out"] = te
         res = evaluate(data, model, te)
