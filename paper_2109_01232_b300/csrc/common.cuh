@@ -18,18 +18,22 @@ constexpr int TILE_MAX = 4096;    // largest SpMV row tile; every buffer's leadi
                                   // is a multiple of it, so tiles never cross the padding
 
 // Precision of the inner cycle: S = storage type of the Krylov basis and of the
-// copy of A, W = working (accumulation) type, VEC = rows per 16-byte vector of S (the
-// CGS update kernels' unit of a thread), VT = rows per lane in the SpMV kernel's dot
-// products (its warp tile is VT slices of 32 rows: 128 rows in every low precision; with
-// 256-row tiles in FP16/BF16 a CTA had fewer tiles than warps on 10^6 rows).
+// copy of A, W = working (accumulation) type, VEC = rows per thread of the CGS update
+// kernels (one or two 16-byte vectors of S), VT = rows per lane in the SpMV kernel's dot
+// products (its warp tile is VT slices of 32 rows: 128 rows in every precision; with
+// 256-row tiles in FP16/BF16 a CTA had fewer tiles than warps on 10^6 rows), RT = rows per
+// thread of the row-tiled SpMV kernels (CSR tile, polynomial, plain SpMV).
+// FP64 takes 4 rows per thread (two 16-byte vectors) in the CGS and dot-product loops: its
+// warp reductions then cost 9 FP64 additions per 8 columns and 128 rows instead of 64, and
+// FP64 arithmetic, not bandwidth, bounds the FP64 cycle on this part.
 template <int P> struct Tr;
 // V_EF: the SpMV kernel reads the old basis columns with the half-evict-first L2 policy
 // (FP64/FP32) or plainly (FP16/BF16: their basis is small enough that keeping all of it in
 // L2 for the CGS kernels measured faster).
-template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 2, VT = 2; static constexpr bool V_EF = true; };
-template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4; static constexpr bool V_EF = true; };
-template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4; static constexpr bool V_EF = false; };
-template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4; static constexpr bool V_EF = false; };
+template <> struct Tr<0> { using S = double;        using W = double; static constexpr int VEC = 4, VT = 4, RT = 2; static constexpr bool V_EF = true; };
+template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4, RT = 4; static constexpr bool V_EF = true; };
+template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4, RT = 4; static constexpr bool V_EF = false; };
+template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4, RT = 4; static constexpr bool V_EF = false; };
 
 // storage -> working type
 // 1 / v for v an exact power of two in the normal range (the basis scale v_scale): the

@@ -422,7 +422,7 @@ __device__ __forceinline__ void update_all(const S* __restrict__ V, long long ld
 template <int P>
 struct SpmvSmem {
   using W = typename Tr<P>::W;
-  static constexpr int TR = NT * Tr<P>::VT;  // rows per CTA tile: VT slices per warp
+  static constexpr int TR = NT * Tr<P>::RT;  // rows per CTA tile: RT rows per thread
   static constexpr int CAP = 4096;  // CSR engine: nonzeros staged per chunk
   // dynamic shared memory of k_spmv_arnoldi (CSR: staged products and row pointers)
   static size_t bytes(int ncol) {
@@ -452,10 +452,10 @@ __global__ void __launch_bounds__(NT) k_spmv_arnoldi(
     typename Tr<P>::W* __restrict__ part, DevState* st, double* __restrict__ h1) {
   using S = typename Tr<P>::S;
   using W = typename Tr<P>::W;
-  constexpr int VEC = Tr<P>::VEC;
+  constexpr int VEC = Tr<P>::RT;  // rows per thread of the tile, also in its dot products
   constexpr int TR = SpmvSmem<P>::TR;
   constexpr int CAP = SpmvSmem<P>::CAP;
-  static_assert(TR == NT * VEC, "the CSR tile's dot layout needs VT == VEC (FP64, FP32)");
+  static_assert(TR == NT * VEC, "the CSR tile's dot layout takes RT rows per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   W* prod_s = reinterpret_cast<W*>(smem_raw);
   W* w_s = prod_s + CAP;
