@@ -34,6 +34,12 @@ template <> struct Tr<0> { using S = double;        using W = double; static con
 template <> struct Tr<1> { using S = float;         using W = float;  static constexpr int VEC = 4, VT = 4, RT = 4; static constexpr bool V_EF = true; };
 template <> struct Tr<2> { using S = __half;        using W = float;  static constexpr int VEC = 8, VT = 4, RT = 4; static constexpr bool V_EF = false; };
 template <> struct Tr<3> { using S = __nv_bfloat16; using W = float;  static constexpr int VEC = 8, VT = 4, RT = 4; static constexpr bool V_EF = false; };
+// FP64 with two rows per thread in the step kernels, for plans too small to give every CTA
+// of the four-row grid its rows (fewer rows per thread spread the FP64 work over more SMs);
+// chosen at plan creation by the row count (solver.cu, fp64_kernel_set).  Not a storage
+// precision of the API: a plan's precision stays GMRES_FP64.
+constexpr int KP_FP64_NARROW = 4;
+template <> struct Tr<KP_FP64_NARROW> { using S = double; using W = double; static constexpr int VEC = 2, VT = 2, RT = 2; static constexpr bool V_EF = true; };
 
 // storage -> working type
 // 1 / v for v an exact power of two in the normal range (the basis scale v_scale): the

@@ -58,6 +58,7 @@ struct PolyOp {
 struct Plan {
   int kind = 1;  // 0: FP64 GMRES, 1: GMRES-IR
   int prec = 1;  // storage precision of the cycle
+  int kp = 1;    // kernel set (Tr index) of the cycle: prec, or KP_FP64_NARROW for small FP64 plans
   gmres_csr A{};
   int n = 0, m = 0;
   long long ld = 0;
@@ -429,15 +430,26 @@ static int configure_residual(Plan& pl) {
   return GMRES_OK;
 }
 
+// Calls f with the Tr index kp (a plan's kernel set) as a compile-time constant.
 template <class F>
-static int dispatch(int prec, F&& f) {
-  switch (prec) {
+static int dispatch(int kp, F&& f) {
+  switch (kp) {
     case GMRES_FP64: return f(std::integral_constant<int, 0>{});
     case GMRES_FP32: return f(std::integral_constant<int, 1>{});
     case GMRES_FP16: return f(std::integral_constant<int, 2>{});
     case GMRES_BF16: return f(std::integral_constant<int, 3>{});
+    case KP_FP64_NARROW: return f(std::integral_constant<int, KP_FP64_NARROW>{});
   }
   return GMRES_ERR_INVALID;
+}
+
+// Kernel set of an FP64 plan with n rows on `sms` SMs.  The four-row step kernels pay off
+// once the FP64 work fills the GPU: below FP64_WIDE_ROWS_PER_SM rows per SM their grid
+// leaves SMs idle or thin (each CTA owns whole 32-thread groups of rows), and the two-row
+// kernels, on twice as many threads, finish a step sooner.
+constexpr long long FP64_WIDE_ROWS_PER_SM = 1024;
+static int fp64_kernel_set(long long n, int sms) {
+  return n >= FP64_WIDE_ROWS_PER_SM * (long long)std::max(sms, 1) ? GMRES_FP64 : KP_FP64_NARROW;
 }
 
 static size_t storage_bytes(int prec) { return prec == 0 ? 8 : prec == 1 ? 4 : 2; }
@@ -596,6 +608,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   int dev = 0;
   if (int e_ = CUDA_STATUS(cudaGetDevice(&dev))) return fail(e_);
   cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, dev);
+  pl->kp = pl->prec == GMRES_FP64 ? fp64_kernel_set(pl->n, pl->sms) : pl->prec;
   if (int e = check_csr_device(A, s)) return fail(e);
   if (p->bj_rcm) {  // from here on the plan works on its reordered copy, pl->A
     auto tr0 = std::chrono::steady_clock::now();
@@ -686,7 +699,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     const int* rp = A->row_ptr;
     const int* ci = A->col_idx;
     const double* va = A->vals;
-    dispatch(pl->prec, [&](auto PP) {
+    dispatch(pl->kp, [&](auto PP) {
       using S = typename Tr<decltype(PP)::value>::S;
       k_build_sell<S><<<blocks, 256, 0, s>>>(rp, ci, va, pl->n, pl->sell_meta, pl->nslices,
                                              pl->a_scale, pl->sell_cols, (S*)pl->sell_vals);
@@ -702,7 +715,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     // the meta upload reads `meta` asynchronously: finish before it goes out of scope
     if (int e_ = CUDA_STATUS(cudaStreamSynchronize(s))) return fail(e_);
   }
-  if ((e = dispatch(pl->prec, [&](auto P) { return configure<decltype(P)::value>(*pl); }))) return fail(e);
+  if ((e = dispatch(pl->kp, [&](auto P) { return configure<decltype(P)::value>(*pl); }))) return fail(e);
   if ((e = configure_residual(*pl))) return fail(e);
   pl->part_step_off = 8 * (size_t)(2 * pl->grid_res + 2);
   const size_t step_parts_n = 2 * (size_t)(m + 2) * pl->grid_spmv + (size_t)(m + 2) * pl->grid_vec;
@@ -755,7 +768,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
     int* d_bad = nullptr;
     if ((e = alloc((void**)&d_bad, sizeof(int)))) return fail(e);
     const int fgrid = (int)std::min<long long>(nblocks, (long long)pl->sms * 16);
-    dispatch(pl->prec, [&](auto PP) {
+    dispatch(pl->kp, [&](auto PP) {
       using W = typename Tr<decltype(PP)::value>::W;
       k_bj_factor<W><<<fgrid, BJ_FACTOR_THREADS, 0, s>>>(A->row_ptr, A->col_idx, A->vals, pl->n,
                                                          pl->bj, (W*)pl->bj_lu, pl->bj_rowp, d_bad);
@@ -804,7 +817,7 @@ int plan_create(Plan** out, const gmres_csr* A, int kind, const gmres_params* p,
   if (int e_ = CUDA_STATUS(cudaEventCreate(&pl->ev1))) return fail(e_);
   if (int e_ = CUDA_STATUS(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal)))
     return fail(e_);
-  dispatch(pl->prec, [&](auto P) {
+  dispatch(pl->kp, [&](auto P) {
     launch_cycle<decltype(P)::value>(*pl, pl->cap);
     return 0;
   });
@@ -905,7 +918,7 @@ int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
   // the polynomial's precision: the plan's, or FP32 for an FP64 plan with poly_in_fp32
-  int e = dispatch(pl.poly32 ? GMRES_FP32 : pl.prec, [&](auto PP) {
+  int e = dispatch(pl.poly32 ? GMRES_FP32 : pl.kp, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using W = typename Tr<P>::W;
     k_load_work<P><<<pl.grid_elem, NT, 0, s>>>(v, (W*)pl.pa, pl.n);
@@ -921,7 +934,7 @@ int plan_poly_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
 // working type, both in the plan's numbering).  Asynchronous on s (two kernels).
 int plan_bj_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
   if (!pl.bj || !v || !y) return GMRES_ERR_INVALID;
-  int e = dispatch(pl.prec, [&](auto PP) {
+  int e = dispatch(pl.kp, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using W = typename Tr<P>::W;
     k_load_work<P><<<pl.grid_elem, NT, 0, s>>>(v, (W*)pl.pa, pl.n);
@@ -936,7 +949,7 @@ int plan_bj_apply(Plan& pl, const double* v, void* y, cudaStream_t s) {
 int plan_spmv(Plan& pl, const double* v, void* y, cudaStream_t s) {
   init_state(pl, *pl.h_st);
   CK(cudaMemcpyAsync(pl.st, pl.h_st, sizeof(DevState), cudaMemcpyHostToDevice, s));
-  int e = dispatch(pl.prec, [&](auto PP) {
+  int e = dispatch(pl.kp, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using S = typename Tr<P>::S;
     using W = typename Tr<P>::W;
@@ -964,7 +977,7 @@ int plan_arnoldi(Plan& pl, const double* v0, int steps, void* V_out, double* H_o
   CK(cudaMemcpyAsync(pl.bb, v0, nb, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(pl.xb, 0, nb, s));
   launch_residual(pl, 1, s);  // r = v0, sigma = 1/||v0||, |g_0| = 1
-  int e = dispatch(pl.prec, [&](auto PP) {
+  int e = dispatch(pl.kp, [&](auto PP) {
     constexpr int P = decltype(PP)::value;
     using S = typename Tr<P>::S;
     using W = typename Tr<P>::W;
@@ -1006,7 +1019,7 @@ int plan_profile_cycle(Plan& pl, const double* b, const double* x0, double* ms_o
   for (auto& e : ev) CK(cudaEventCreate(&e));
   std::vector<int> ran(nslots, 0);
   int* h_flag = &pl.h_st->cycle_done;
-  int err = dispatch(pl.prec, [&](auto PP) -> int {
+  int err = dispatch(pl.kp, [&](auto PP) -> int {
     constexpr int P = decltype(PP)::value;
     for (int j = 0; j < m; ++j) {
       for (int w = 0; w < 3; ++w) {
@@ -1073,7 +1086,7 @@ int plan_profile_cycle_graph(Plan& pl, const double* b, const double* x0, double
   if ((err = CUDA_STATUS(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))) return done(err);
   if ((err = CUDA_STATUS(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))))
     return done(err);
-  dispatch(pl.prec, [&](auto PP) -> int {
+  dispatch(pl.kp, [&](auto PP) -> int {
     constexpr int P = decltype(PP)::value;
     for (int j = 0; j < m; ++j)
       for (int w = 0; w < 3; ++w) {
@@ -1197,10 +1210,10 @@ int gmres_plan_spmv_timed(gmres_plan plan, const void* x, void* y, int32_t reps,
                                                 pl.nslices, pl.n, pl.a_scale, (const W*)x, (W*)y);
     return 0;
   };
-  gm::dispatch(pl.prec, launch);  // warm-up
+  gm::dispatch(pl.kp, launch);  // warm-up
   CK(cudaGetLastError());
   CK(cudaEventRecord(pl.ev0, s));
-  for (int r = 0; r < reps; ++r) gm::dispatch(pl.prec, launch);
+  for (int r = 0; r < reps; ++r) gm::dispatch(pl.kp, launch);
   CK(cudaEventRecord(pl.ev1, s));
   CK(cudaGetLastError());
   CK(cudaEventSynchronize(pl.ev1));

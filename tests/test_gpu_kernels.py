@@ -113,15 +113,24 @@ def _column_errors(Vg, H, Vo, Ho, nA):
     return dV, dH
 
 
-@pytest.mark.parametrize("which", ["2d", "3d", "2d130", "3d27"])
+# FP64 plans with at least 1024 rows per SM run the step kernels with four rows per thread,
+# smaller ones with two: 3d56 (175,616 rows) takes the four-row kernels on a 148-SM B300.
+FP64_WIDE = {"3d56": lambda: gen.conv_diff_3d(56, 10.0, (1.0, -2.0, 0.5))}
+
+
+@pytest.mark.parametrize("which", ["2d", "3d", "2d130", "3d27", "3d56"])
 def test_arnoldi_fp64_matches_oracle(g, torch, which):
     """FP64 Arnoldi/CGS2 (Algorithm 1, Section 3.1) against the oracle, every column of V
     and H to 1e-13 (normwise, H relative to ||A||).  The two differ only in the order of
     their sums; measured on a B300 the gap grows from ~1e-16 to ~4e-15 (V) and stays below
     2e-16 ||A|| (H) over 50 steps, the same size as the oracle's own spread when its start
-    vector is perturbed by one unit roundoff."""
-    p = (PROBLEMS.get(which) or LARGE[which])()
-    steps = 30 if which in PROBLEMS else 50
+    vector is perturbed by one unit roundoff.  Both FP64 kernel sets are covered (two rows
+    per thread below 1024 rows per SM, four above)."""
+    p = (PROBLEMS.get(which) or LARGE.get(which) or FP64_WIDE[which])()
+    if which in FP64_WIDE:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert p.n >= 1024 * sms  # the four-row kernels run
+    steps = 30 if which in PROBLEMS or which in FP64_WIDE else 50
     A, plan = _plan(g, p, "fp64", m=steps)
     v0 = oracle.splitmix64_uniform(5, p.n)
     V, H, k = plan.arnoldi(torch.tensor(v0, device="cuda"), steps)
