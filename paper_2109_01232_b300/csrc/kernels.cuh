@@ -332,91 +332,118 @@ __device__ __forceinline__ void dot_cols(const S* __restrict__ V, long long ld, 
   }
 }
 
-// Warp totals of 8 columns at once.  d[b] is this lane's term of column b; returns, in
-// every lane, the warp total of column (lane >> 2) & 7.  Each exchange (xor 16, 8, 4)
-// sends the half of the columns that the partner keeps, halving what a lane carries, then
-// two plain butterfly steps (xor 2, 1) finish: 9 shuffles instead of 8 x 5.  Every total
-// is formed by the same additions, with the same operands, as warp_sum of that column
-// (own value + partner's, partners xor 16, 8, 4, 2, 1), so the totals are bitwise
-// warp_sum's.
-template <class W>
-__device__ __forceinline__ W warp_sum8_cols(const W (&d)[8]) {
+// Warp totals of K = 2, 4 or 8 columns at once.  d[b] is this lane's term of column b;
+// returns, in every lane, the warp total of column lane >> (5 - log2 K) (for K = 8: (lane >>
+// 2) & 7).  Each of the first log2 K exchanges (xor 16, 8, 4) sends the half of the columns
+// that the partner keeps, halving what a lane carries; plain butterfly steps finish (9
+// shuffles instead of 8 x 5 for K = 8).  Every total is formed by the same additions, with
+// the same operands, as warp_sum of that column (own value + partner's, partners xor 16, 8,
+// 4, 2, 1), so the totals are bitwise warp_sum's.
+template <int K, class W>
+__device__ __forceinline__ W warp_sum_cols(const W (&d)[K]) {
+  static_assert(K == 2 || K == 4 || K == 8, "2, 4 or 8 columns");
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
-  W h[4];  // columns 4 b4 + i
+  W h[K];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const W send = b4 ? d[i] : d[4 + i];
-    const W keep = b4 ? d[4 + i] : d[i];
-    h[i] = keep + __shfl_xor_sync(full, send, 16);
-  }
-  W q[2];  // columns 4 b4 + 2 b3 + i
+  for (int b = 0; b < K; ++b) h[b] = d[b];
+  int o = 16;
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const W send = b3 ? h[i] : h[2 + i];
-    const W keep = b3 ? h[2 + i] : h[i];
-    q[i] = keep + __shfl_xor_sync(full, send, 8);
+  for (int half = K / 2; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;  // this lane keeps the upper half of its columns
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const W send = up ? h[i] : h[half + i];
+      const W keep = up ? h[half + i] : h[i];
+      h[i] = keep + __shfl_xor_sync(full, send, o);
+    }
   }
-  const W send = b2 ? q[0] : q[1];
-  W v = (b2 ? q[1] : q[0]) + __shfl_xor_sync(full, send, 4);  // column 4 b4 + 2 b3 + b2
-  v += __shfl_xor_sync(full, v, 2);
-  v += __shfl_xor_sync(full, v, 1);
+  W v = h[0];
+#pragma unroll
+  for (; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
   return v;
 }
 
-// Dot products of w with the columns V[c0..nc) for this thread's rows, summed over the
-// warp and added to acc[c] by one lane per column (always the same lane for a column).
-// EF: see update_cols.
-template <bool EF, class S, class W, int VEC>
-__device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long ld, long long base,
-                                            int nc, const W (&wv)[VEC], W* acc, int c0 = 0) {
+// Dot products of w with the K columns V[c .. c+K) for this thread's rows, summed over the
+// warp and added to acc: column c + b's total by one lane, always the same lane for a given
+// K and b.  K loads per thread in flight.  EF: see update_cols.
+template <int K, bool EF, class S, class W, int VEC>
+__device__ __forceinline__ void dots_block(const S* __restrict__ V, long long ld, long long base,
+                                           int c, const W (&wv)[VEC], W* acc) {
   const int lane = threadIdx.x & 31;
-  int c = c0;
-  for (; c + 8 <= nc; c += 8) {
-    W d[8];
-    dot_cols<8, EF>(V, ld, base, c, wv, d);
-    const W t = warp_sum8_cols(d);
-    if ((lane & 3) == 0) acc[c + (lane >> 2)] += t;
-  }
-  for (; c < nc; ++c) {
-    W d[1];
-    dot_cols<1, EF>(V, ld, base, c, wv, d);
+  W d[K];
+  dot_cols<K, EF>(V, ld, base, c, wv, d);
+  if constexpr (K == 1) {
     const W t = warp_sum(d[0]);
     if (lane == 0) acc[c] += t;
+  } else {
+    constexpr int SH = K == 2 ? 4 : K == 4 ? 3 : 2;  // lane >> SH: the column this lane holds
+    const W t = warp_sum_cols<K>(d);
+    if ((lane & ((1 << SH) - 1)) == 0) acc[c + (lane >> SH)] += t;
   }
 }
 
-// dots_to_acc over V[0..nc) with the columns taken in descending order (the same value
-// per column).  k_cgs_u1 calls it right after update_all has loaded the same columns in
-// ascending order, so the newest lines, the likeliest to still be in L1, are read first.
+// Dot products of w with the columns V[c0..nc) for this thread's rows, summed over the
+// warp and added to acc[c]: blocks of 8 columns, then at most one block each of 4, 2 and 1
+// (one round of loads per block instead of one per leftover column).  EF: see update_cols.
+template <bool EF, class S, class W, int VEC>
+__device__ __forceinline__ void dots_to_acc(const S* __restrict__ V, long long ld, long long base,
+                                            int nc, const W (&wv)[VEC], W* acc, int c0 = 0) {
+  int c = c0;
+  for (; c + 8 <= nc; c += 8) dots_block<8, EF>(V, ld, base, c, wv, acc);
+  if (nc - c >= 4) {
+    dots_block<4, EF>(V, ld, base, c, wv, acc);
+    c += 4;
+  }
+  if (nc - c >= 2) {
+    dots_block<2, EF>(V, ld, base, c, wv, acc);
+    c += 2;
+  }
+  if (c < nc) dots_block<1, EF>(V, ld, base, c, wv, acc);
+}
+
+// dots_to_acc over V[0..nc) with the columns taken newest first (the same value per
+// column).  k_cgs_u1 calls it right after update_all has loaded the same columns in
+// ascending order, so the newest lines, the likeliest to still be in L1, are read first:
+// the leftover blocks (1, 2, 4 columns) from the top, then the blocks of 8 downwards.
 template <class S, class W, int VEC>
 __device__ __forceinline__ void dots_to_acc_desc(const S* __restrict__ V, long long ld,
                                                  long long base, int nc, const W (&wv)[VEC],
                                                  W* acc) {
-  const int lane = threadIdx.x & 31;
   int c = nc;
-  for (; c > (nc & ~7); --c) {
-    W d[1];
-    dot_cols<1, false>(V, ld, base, c - 1, wv, d);
-    const W t = warp_sum(d[0]);
-    if (lane == 0) acc[c - 1] += t;
+  const int r = nc & 7;
+  if (r & 1) {
+    c -= 1;
+    dots_block<1, false>(V, ld, base, c, wv, acc);
   }
-  for (; c >= 8; c -= 8) {
-    W d[8];
-    dot_cols<8, false>(V, ld, base, c - 8, wv, d);
-    const W t = warp_sum8_cols(d);
-    if ((lane & 3) == 0) acc[c - 8 + (lane >> 2)] += t;
+  if (r & 2) {
+    c -= 2;
+    dots_block<2, false>(V, ld, base, c, wv, acc);
   }
+  if (r & 4) {
+    c -= 4;
+    dots_block<4, false>(V, ld, base, c, wv, acc);
+  }
+  for (; c >= 8; c -= 8) dots_block<8, false>(V, ld, base, c - 8, wv, acc);
 }
 
 // w -= V[0..nc) coef for this thread's rows.  EF: see update_cols.
+// Blocks of 8 columns, then at most one block each of 4, 2 and 1, in ascending order (every
+// row's products are subtracted in column order whatever the blocking).
 template <bool EF, class S, class W, int VEC>
 __device__ __forceinline__ void update_all(const S* __restrict__ V, long long ld, long long base,
                                            int nc, const W* __restrict__ coef, W (&wv)[VEC]) {
   int c = 0;
   for (; c + 8 <= nc; c += 8) update_cols<8, EF>(V, ld, base, c, coef, wv);
-  for (; c < nc; ++c) update_cols<1, EF>(V, ld, base, c, coef, wv);
+  if (nc - c >= 4) {
+    update_cols<4, EF>(V, ld, base, c, coef, wv);
+    c += 4;
+  }
+  if (nc - c >= 2) {
+    update_cols<2, EF>(V, ld, base, c, coef, wv);
+    c += 2;
+  }
+  if (c < nc) update_cols<1, EF>(V, ld, base, c, coef, wv);
 }
 
 template <int P>
