@@ -372,8 +372,9 @@ typedef struct gmres_batch_plan_s* gmres_batch_plan;
 /* Creates the workspace (FP32 copy of the values, per-cluster basis and vectors), chooses
  * the CTA size (256 or 512 threads) and the cluster size (1, 2, 4 or 8 CTAs per system) --
  * if autotune is nonzero by timing each pair on a sample of the systems (every 8th by
- * size, b = ones), else 256 threads in clusters of 4 -- and captures the launch as a CUDA
- * graph.  p: restart_m (<= GMRES_BATCH_MAX_M), rtol, inner_rtol, max_iters (per system),
+ * size, b = ones) and the two fastest once more on all the systems (two extra solves of
+ * the whole batch at set-up), else 256 threads in clusters of 4 -- and captures the launch
+ * as a CUDA graph.  p: restart_m (<= GMRES_BATCH_MAX_M), rtol, inner_rtol, max_iters (per system),
  * inner_prec (GMRES_FP32, or GMRES_FP64 for plain FP64 GMRES(m) per system).
  * Errors: INVALID (bad sizes/offsets/structure/params), TOO_LARGE (m), OOM, CUDA. */
 int gmres_batch_plan_create(gmres_batch_plan* plan, const gmres_csr_batch* A,
