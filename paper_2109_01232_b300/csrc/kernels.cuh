@@ -965,10 +965,10 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 2) k_spmv_sell(
     W nrm = W(0);
 #pragma unroll
     for (int q = 0; q < VEC; ++q) nrm += wv[q] * wv[q];
-    // columns 0..j-1 are read-only here (half evict-first in FP64/FP32, see Tr::V_EF);
-    // column j was just stored by the warp
-    dots_to_acc<Tr<P>::V_EF, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j, wv, acc);
-    dots_to_acc<false, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc, j);
+    // columns 0..j (half evict-first in FP64/FP32, see Tr::V_EF); column j, just stored by
+    // the warp, goes into the last block with the old ones (one round of loads less than a
+    // block of its own; its products and sums are the same)
+    dots_to_acc<Tr<P>::V_EF, S, W, VEC>(V, ld, (long long)r0 + VEC * lane, j + 1, wv, acc);
     nrm = warp_sum(nrm);
     if (lane == 0) acc[j + 1] += nrm;
   }
